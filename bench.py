@@ -1,0 +1,277 @@
+"""Benchmark: the whole traveltime-parameter search on the 200-CMP line.
+
+One step = one complete search (tt_search) over every zero-offset sample of
+a 200-CMP x 48-offset x 1500-sample line (300,000 domains): DE with NP = 64,
+NG = 100, F = 0.5, CR = 0.9, the neighbour exchange every 10 generations
+and 5 gradient-polish steps, i.e. every row of the hot path. Inputs are
+resident on the device when the timed region starts; between timed steps
+L2 is flushed by writing a 256 MiB buffer (the line itself, 59 MB, fits in
+L2).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (launched by torchrun): every rank solves its own independent line
+(a replica with its own seed; the search has no cross-line exchange), so
+per-GPU work is fixed and scaling is weak. Rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (FP64 semblance, FP32 DE) on the host
+cores instead, each step a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ZO samples solved/s (CRS search with neighbour exchange + gradient polish)"
+UNIT = "ZO samples/s"
+FLOPS_PER_TRACE_EVAL = 75          # see the design doc, kernel K1
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def workload_config(wl, n_gpus):
+    p = wl.problem
+    return {"workload": "CRS line 200 CMP x 48 offsets x 1500 samples (dt 4 ms), "
+                        "aperture +-10 CMP, window 11",
+            "n_dom": p.n_dom, "np": wl.de.np, "ng": wl.de.ng, "exch_every": wl.de.exch_every,
+            "polish_steps": wl.de.polish_steps, "storage": wl.storage,
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "1 GPU"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_median": float(np.median([float(r[3]) for r in rows
+                                                   if r[3].replace(".", "").isdigit()] or [0]))}
+
+
+# ------------------------------------------------------------------ oracle legs
+
+def oracle_sample(wl, n_m0=2, n_t0=2, c0=99, it0=600):
+    """A bounded sample of the workload for the CPU oracle: an n_m0 x n_t0
+    block of domains in the middle of the line, with the full search
+    settings (exchange inside the block)."""
+    import synth
+    return synth.line_problem(wl.line, half_window=5, ap_half=10,
+                              cmps=list(range(c0, c0 + n_m0)), t0_range=(it0, it0 + n_t0))
+
+
+def time_oracle(wl, prob):
+    import oracle
+    t = time.perf_counter()
+    oracle.search.search(wl.traces, wl.mid, wl.off, prob, wl.de)
+    return time.perf_counter() - t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from synth import configs
+    wl = configs.crs_line(0)
+    prob = oracle_sample(wl, 1, 2)
+    for _ in range(args.warmup):
+        time_oracle(wl, prob)
+    ts = [time_oracle(wl, prob) for _ in range(args.steps)]
+    per = float(np.mean(ts))
+    value = prob.n_dom / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{prob.n_dom} domains (1 CMP x 2 samples at CMP 99, "
+                                       "it0 600-601) per step, full NP/NG/exchange/polish"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    from paper_2304_11399_gb300 import build as _build
+    _build.build()
+    import paper_2304_11399_gb300 as tt
+    from synth import configs
+
+    wl = configs.crs_line(rank)
+    wl.storage = args.storage
+    prob = wl.problem
+    # CPU baseline first (rank 0, N = 1): the oracle as it stands on a sample
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sp = oracle_sample(wl)
+        secs = time_oracle(wl, sp)
+        cpu = {"value": sp.n_dom / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{sp.n_dom} domains (2 CMP x 2 samples at CMP 99-100, it0 600-601), "
+                         f"full NP/NG/exchange/polish, {secs:.1f} s single-threaded numpy"}
+
+    stream = torch.cuda.current_stream()
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, storage=args.storage,
+                           device=dev)
+    best_t = torch.empty((prob.n_dom, 3), dtype=torch.float32, device=dev)
+    best_s = torch.empty((prob.n_dom,), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 18, dtype=torch.float32, device=dev)  # 256 MiB
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        tt.tt_search(ctx, best_t, best_s)
+    barrier()
+    tt.tt_ctx_profile(ctx, True)
+    tt.tt_ctx_stats(ctx, reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    n_evals = 0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        _, _, n_evals = tt.tt_search(ctx, best_t, best_s)
+        ev[k][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    stats = tt.tt_ctx_stats(ctx, reset=True)
+    tt.tt_ctx_profile(ctx, False)
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    per_step_s = ms_max / 1e3 / args.steps
+    value = world * prob.n_dom / per_step_s
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_tr = torch.from_numpy(wl.traces).pin_memory()
+        host_bt = torch.empty((prob.n_dom, 3), dtype=torch.float32).pin_memory()
+        host_bs = torch.empty((prob.n_dom,), dtype=torch.float32).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            tt.tt_ctx_load_traces(ctx, host_tr)
+            tt.tt_search(ctx, best_t, best_s)
+            host_bt.copy_(best_t, non_blocking=True)
+            host_bs.copy_(best_s, non_blocking=True)
+            torch.cuda.synchronize()
+        barrier()
+        e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(e_s, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * prob.n_dom * args.steps / float(e_s.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(wl.traces.nbytes),
+               "d2h_bytes_per_step": int(host_bt.numel() * 4 + host_bs.numel() * 4)}
+
+    # roofline of the dominant kernel (semblance), from its live launch times
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = None
+    if stats["timed_launches"] > 0 and stats["semblance_ms"] > 0:
+        flops = stats["trace_evals"] * FLOPS_PER_TRACE_EVAL
+        n_l = stats["semblance_launches"]
+        achieved = (flops / n_l) / (stats["semblance_ms"] / stats["timed_launches"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_semblance (FP32 FMA pipe; peak = 152 SM x 128 lanes x 2 x 2070 MHz)",
+                "per_launch_ms": stats["semblance_ms"] / stats["timed_launches"],
+                "trace_evals_per_s": stats["trace_evals"] / (stats["semblance_ms"] / 1e3),
+                "semblance_share_of_step": stats["semblance_ms"] / ms}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.storage == "f32" else "bf16-stored/f32",
+                "data": "synthetic (seeded Ricker events + Gaussian noise, SNR 3)",
+                "config": workload_config(wl, world), "clocks": clk, "e2e": e2e,
+                "gpu_launches": int(stats["launches"]), "semblance_calls_per_step": n_evals,
+                "roofline": roof, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+/*
+ * tt.h -- C ABI of libtt, a GPU (sm_103a) traveltime-parameter search.
+ *
+ * The library evaluates the semblance coherence of a traveltime operator
+ * over prestack seismic gathers and searches the operator's parameters with
+ * differential evolution plus an exchange of best individuals between
+ * neighbouring zero-offset samples (evolution by neighborhood similarity),
+ * after "Ultra-fast traveltime parameters search by a coevolutionary
+ * optimization approach using GPUs" (arXiv 2304.11399).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless a
+ *    comment says "host". Float arrays are IEEE float32, row-major, densely
+ *    packed, with the shapes given in brackets.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). All work is enqueued on it and the call returns without
+ *    waiting, except tt_ctx_create / tt_ctx_load_traces (which synchronise
+ *    the stream before returning) and where stated.
+ *  - No entry point other than tt_ctx_create allocates device memory.
+ *  - Every entry point returns a tt_status; on failure nothing has been
+ *    written to caller arrays unless the failure is TT_ERR_CUDA raised by an
+ *    asynchronous launch. tt_last_error() gives a message.
+ *  - A context may be used from one host thread at a time; calls on
+ *    different streams that share a context's scratch (tt_search,
+ *    tt_neighbor_exchange) must not overlap.
+ *
+ * Notation (the paper's): a domain is one zero-offset sample (m0, it0),
+ * t0 = it0 dt (Sec. 2.1, "index-vector point (t, tr)"); its aperture is the
+ * set of N traces used by one semblance call (T_a in eq. order); theta is a
+ * parameter vector ("individual", Sec. 2) of D = 1 (CMP: C) or D = 3
+ * (ZO-CRS: A, B, C) values; NP individuals form a domain's population.
+ */
+#ifndef TT_H
+#define TT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tt_status;
+enum {
+  TT_OK = 0,
+  TT_ERR_INVALID_ARG = 1,   /* bad pointer, size, index or configuration   */
+  TT_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed        */
+  TT_ERR_OUT_OF_MEMORY = 3, /* tt_ctx_create could not allocate            */
+  TT_ERR_TIMEOUT = 4,       /* a bounded device wait gave up               */
+  TT_ERR_UNSUPPORTED = 5    /* valid request outside what is built         */
+};
+
+/* Traveltime operators (readings of the operators the paper cites, Sec. 1):
+ *   TT_OP_CMP:  T = t0^2 + C h^2                          theta = (C)
+ *   TT_OP_CRS:  T = (t0 + A dm)^2 + B dm^2 + C h^2        theta = (A, B, C)
+ * with dm = m - m0 the midpoint displacement and h the full offset of a
+ * trace (metres), t = sqrt(T) (seconds); a trace with T < 0 contributes
+ * zero amplitudes and still counts in N. */
+enum { TT_OP_CMP = 0, TT_OP_CRS = 1 };
+
+/* Storage type of the context's copy of the traces (arithmetic is FP32). */
+enum { TT_STORE_F32 = 0, TT_STORE_BF16 = 1 };
+
+#define TT_MAX_DIM 8
+#define TT_MAX_HALF_WINDOW 8
+
+/* Prestack gathers (Sec. 4, "bucket": the traces of an interactive domain). */
+typedef struct tt_gathers {
+  int32_t n_traces;      /* number of traces                                 */
+  int32_t ns;            /* samples per trace (NT)                           */
+  int32_t storage;       /* TT_STORE_F32 or TT_STORE_BF16                    */
+  int32_t reserved;
+  const float* traces;   /* [n_traces][ns] amplitudes; the record is zero    */
+                         /* outside samples 0..ns-1                          */
+  const float* mid;      /* [n_traces] midpoint m of each trace (m)          */
+  const float* off;      /* [n_traces] full source-receiver offset h (m)     */
+} tt_gathers;
+
+/* Domains and apertures. Domains sharing a midpoint, sample interval and
+ * aperture form a group; apertures are CSR lists of trace indices. */
+typedef struct tt_problem {
+  int32_t op;            /* TT_OP_CMP or TT_OP_CRS                           */
+  int32_t half_window;   /* w: the window is the 2w+1 samples t + k dt,      */
+                         /* k = -w..w (Sec. 2, W_l = 2w+1), 0 <= w <= 8      */
+  int32_t n_groups;
+  int32_t n_dom;
+  const float* group_m0;    /* [n_groups] reference midpoint m0 (m)          */
+  const float* group_dt;    /* [n_groups] sample interval dt (s), > 0        */
+  const int32_t* ap_ptr;    /* [n_groups+1] CSR row pointers into ap_idx     */
+  const int32_t* ap_idx;    /* [ap_ptr[n_groups]] trace indices              */
+  const int32_t* dom_it0;   /* [n_dom] zero-offset sample index it0          */
+  const int32_t* dom_group; /* [n_dom] group of each domain                  */
+  int32_t n_m0, n_t0;    /* exchange grid: if n_m0 * n_t0 == n_dom the       */
+                         /* domains are laid out m0-major, d = im0*n_t0+it;  */
+                         /* 0, 0 = no grid (no exchange)                     */
+} tt_problem;
+
+/* Search settings (Sec. 2.1: NP, NG; F, CR held fixed; p = 1). */
+typedef struct tt_de_cfg {
+  int32_t np;            /* population size NP, 4..1024                     */
+  int32_t ng;            /* generations NG >= 0                             */
+  float F, CR;           /* mutation factor, crossover rate in [0, 1]       */
+  uint64_t seed;         /* Philox4x32-10 key                               */
+  float lo[TT_MAX_DIM];  /* parameter bounds, lo[d] <= hi[d]                */
+  float hi[TT_MAX_DIM];
+  int32_t exch_every;    /* neighbour exchange after the selection of every */
+                         /* exch_every-th generation; 0 = never             */
+  int32_t polish_steps;  /* projected gradient-ascent steps after DE        */
+  float polish_lr;       /* step: theta += lr (hi-lo)^2 dS/dtheta           */
+  int32_t reserved;
+} tt_de_cfg;
+
+typedef struct tt_ctx tt_ctx;
+
+/* Message of the last failure on `ctx` (or of the calling thread's last
+ * tt_ctx_create failure when ctx is NULL). Never NULL. */
+const char* tt_last_error(const tt_ctx* ctx);
+
+/* Version string of the library build. */
+const char* tt_version(void);
+
+/* Create a context: validates the problem on the device, copies the traces
+ * into a zero-padded, aligned device layout of the chosen storage type,
+ * builds the per-aperture geometry table, copies the domain arrays and
+ * allocates the search scratch (sized by cfg->np and D). The caller's
+ * arrays may be freed once this returns. Synchronises `stream`.
+ * Errors: INVALID_ARG (NULL pointers, sizes, out-of-range indices, an
+ * unsorted ap_ptr, dt <= 0, bad cfg), OUT_OF_MEMORY, CUDA. On failure
+ * *out is NULL. `cfg` may be NULL when no search will be run. */
+tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* gathers, const tt_problem* problem,
+                        const tt_de_cfg* cfg, void* stream);
+
+/* Reload the context's copy of the traces from `traces` ([n_traces][ns],
+ * same shape as at creation); `host` != 0 means a host pointer (pinned
+ * memory gives an asynchronous-speed copy). Synchronises `stream`. */
+tt_status tt_ctx_load_traces(tt_ctx* ctx, const float* traces, int32_t host, void* stream);
+
+void tt_ctx_destroy(tt_ctx* ctx);
+
+/* Semblance (Sec. 1, Neidell-Taner; Sec. 2.2 eq. S, values in [0, 1]) of P
+ * parameter vectors at every domain:
+ *   u_i = sqrt(T_i)/dt, j = floor(u_i), f = u_i - j,
+ *   a_ik = (1-f) x_i[j+k] + f x_i[j+k+1], k = -w..w,
+ *   S = sum_k (sum_i a_ik)^2 / (N sum_ik a_ik^2), 0 when the energy is 0.
+ * theta [n_dom][P][D], S [n_dom][P]. P >= 1. FP32 arithmetic. */
+tt_status tt_semblance_eval(tt_ctx* ctx, const float* theta, int32_t P, float* S, void* stream);
+
+/* Semblance and its gradient dS/dtheta (an addition to the paper's method,
+ * used to polish the DE winner) by the adjoint of the interpolation and
+ * traveltime: inside an interpolation cell da_ik/du_i = x_i[j+k+1]-x_i[j+k].
+ * theta [n_dom][P][D], S [n_dom][P], dS [n_dom][P][D]. */
+tt_status tt_semblance_grad(tt_ctx* ctx, const float* theta, int32_t P, float* S, float* dS,
+                            void* stream);
+
+/* One differential-evolution step per domain (Sec. 2.1.1-2.1.4, p = 1):
+ *  gen == 0:  initialise pop [n_dom][NP][D] uniformly in [lo, hi]; other
+ *             arrays are ignored and may be NULL.
+ *  gen >= 1:  if trial != NULL, greedy selection: member i takes
+ *             (trial[i], trial_fit[i]) when trial_fit[i] >= fit[i] (NaN
+ *             ranks lowest); then best_idx[d] = argmax fit (lowest index on
+ *             ties); then, if next_trial != NULL, DE/current-to-best/1/bin:
+ *             v = x_i + F (x_best - x_i) + F (x_r1 - x_r2), binomial
+ *             crossover with j_rand, repair v<lo -> (lo+x_i)/2,
+ *             v>hi -> (hi+x_i)/2, written to next_trial [n_dom][NP][D].
+ * Random numbers: Philox4x32-10, key = seed, counter = (i, gen, domain,
+ * block); FP32 arithmetic with one rounding per operation, so results are
+ * bit-reproducible. pop and fit [n_dom][NP] are updated in place;
+ * best_idx [n_dom] may be NULL. */
+tt_status tt_de_step(tt_ctx* ctx, int32_t gen, float* pop, float* fit, const float* trial,
+                     const float* trial_fit, float* next_trial, int32_t* best_idx,
+                     void* stream);
+
+/* best_theta [n_dom][D] and best_S [n_dom] (either may be NULL) = the
+ * member with the highest fitness of each domain (lowest index on ties). */
+tt_status tt_best_snapshot(tt_ctx* ctx, const float* pop, const float* fit, float* best_theta,
+                           float* best_S, void* stream);
+
+/* Neighbour exchange (Sec. 3.4 "Information propagation"): on the m0-major
+ * grid n_m0 x n_t0 (n_m0 * n_t0 == n_dom), every domain imports the
+ * snapshot best_theta [n_dom][D] of its present neighbours, in the order
+ * (it0-1), (it0+1), (m0-1), (m0+1), into its worst members ranked by
+ * (fitness ascending, index ascending) excluding its own best, and
+ * evaluates each import's semblance at its own (m0, t0) into fit.
+ * imports [n_dom][4][D] and slots [n_dom][4] (-1 = absent neighbour)
+ * record what was done; either may be NULL. */
+tt_status tt_neighbor_exchange(tt_ctx* ctx, int32_t n_m0, int32_t n_t0, const float* best_theta,
+                               float* pop, float* fit, float* imports, int32_t* slots,
+                               void* stream);
+
+/* Projected gradient ascent from theta [n_dom][D] (in/out): `steps`
+ * iterations of theta <- clip(theta + lr (hi-lo)^2 dS/dtheta, lo, hi),
+ * S evaluated at every iterate, keeping the best iterate (first on ties);
+ * S [n_dom] receives its semblance. Uses the context's scratch. */
+tt_status tt_polish(tt_ctx* ctx, float* theta, float* S, int32_t steps, float lr, void* stream);
+
+/* Counters of a context, accumulated on the host since the last reset:
+ * `launches` = kernels this context enqueued; `semblance_launches` and
+ * `trace_evals` = semblance/gradient launches and the (aperture trace x
+ * parameter vector) pairs they evaluated; `semblance_ms` = their summed
+ * device time, measured with CUDA events recorded on the launching stream
+ * around each of them while profiling is enabled (0 otherwise). */
+typedef struct tt_stats {
+  uint64_t launches;
+  uint64_t semblance_launches;
+  double trace_evals;
+  double semblance_ms;
+  uint64_t timed_launches;   /* semblance launches covered by semblance_ms */
+} tt_stats;
+
+/* Enable (1) or disable (0) event timing of semblance launches. Enabling
+ * creates a fixed pool of events (no device memory); launches beyond the
+ * pool between two tt_ctx_stats calls are counted but not timed. */
+tt_status tt_ctx_profile(tt_ctx* ctx, int32_t enable);
+
+/* Copy the counters to *out (host) and, if `reset`, zero them. When timed
+ * launches are pending this waits for the last recorded event. */
+tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
+
+/* The whole search (JADE loop of Sec. 2.1 with the exchange of Sec. 3.4):
+ * init, NG generations of select/mutate/evaluate, an exchange after every
+ * exch_every-th selection, then cfg polish_steps of polishing. Writes
+ * best_theta [n_dom][D] and best_S [n_dom] (device). *n_evals (host, may be
+ * NULL) receives the number of semblance evaluations issued:
+ * NP (1 + NG) n_dom (eq. jade_semblance) + imports + polish calls.
+ * Requires a cfg at tt_ctx_create. Uses the context's scratch. */
+tt_status tt_search(tt_ctx* ctx, float* best_theta, float* best_S, uint64_t* n_evals,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TT_H */

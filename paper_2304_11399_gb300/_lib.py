@@ -1,0 +1,93 @@
+"""ctypes view of the C ABI declared in include/tt.h (no logic here)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtt.so")
+
+TT_OK, TT_ERR_INVALID_ARG, TT_ERR_CUDA, TT_ERR_OUT_OF_MEMORY, TT_ERR_TIMEOUT, \
+    TT_ERR_UNSUPPORTED = range(6)
+TT_OP_CMP, TT_OP_CRS = 0, 1
+TT_STORE_F32, TT_STORE_BF16 = 0, 1
+TT_MAX_DIM = 8
+
+STATUS_NAMES = {0: "TT_OK", 1: "TT_ERR_INVALID_ARG", 2: "TT_ERR_CUDA",
+                3: "TT_ERR_OUT_OF_MEMORY", 4: "TT_ERR_TIMEOUT", 5: "TT_ERR_UNSUPPORTED"}
+
+# every function the header declares: name -> (restype, argtypes)
+P = C.c_void_p
+I32 = C.c_int32
+
+
+class Gathers(C.Structure):
+    _fields_ = [("n_traces", I32), ("ns", I32), ("storage", I32), ("reserved", I32),
+                ("traces", P), ("mid", P), ("off", P)]
+
+
+class ProblemT(C.Structure):
+    _fields_ = [("op", I32), ("half_window", I32), ("n_groups", I32), ("n_dom", I32),
+                ("group_m0", P), ("group_dt", P), ("ap_ptr", P), ("ap_idx", P),
+                ("dom_it0", P), ("dom_group", P), ("n_m0", I32), ("n_t0", I32)]
+
+
+class DECfg(C.Structure):
+    _fields_ = [("np", I32), ("ng", I32), ("F", C.c_float), ("CR", C.c_float),
+                ("seed", C.c_uint64), ("lo", C.c_float * TT_MAX_DIM),
+                ("hi", C.c_float * TT_MAX_DIM), ("exch_every", I32), ("polish_steps", I32),
+                ("polish_lr", C.c_float), ("reserved", I32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("semblance_launches", C.c_uint64),
+                ("trace_evals", C.c_double), ("semblance_ms", C.c_double),
+                ("timed_launches", C.c_uint64)]
+
+
+SIGNATURES = {
+    "tt_last_error": (C.c_char_p, [P]),
+    "tt_version": (C.c_char_p, []),
+    "tt_ctx_create": (I32, [C.POINTER(P), C.POINTER(Gathers), C.POINTER(ProblemT),
+                            C.POINTER(DECfg), P]),
+    "tt_ctx_load_traces": (I32, [P, P, I32, P]),
+    "tt_ctx_destroy": (None, [P]),
+    "tt_semblance_eval": (I32, [P, P, I32, P, P]),
+    "tt_semblance_grad": (I32, [P, P, I32, P, P, P]),
+    "tt_de_step": (I32, [P, I32, P, P, P, P, P, P, P]),
+    "tt_best_snapshot": (I32, [P, P, P, P, P, P]),
+    "tt_neighbor_exchange": (I32, [P, I32, I32, P, P, P, P, P, P]),
+    "tt_polish": (I32, [P, P, P, I32, C.c_float, P]),
+    "tt_search": (I32, [P, P, P, C.POINTER(C.c_uint64), P]),
+    "tt_ctx_profile": (I32, [P, I32]),
+    "tt_ctx_stats": (I32, [P, C.POINTER(Stats), I32]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load libtt.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libtt.so is not built ({p}); run __graft_entry__.build() — "
+                           "there is no CPU fallback")
+    lib = C.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def header_declarations(header_path: str) -> list[str]:
+    """Names of the functions declared in a C header (for export checks)."""
+    import re
+    txt = open(header_path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(tt_[a-z_0-9]+)\s*\(", txt, flags=re.M)

@@ -1,0 +1,149 @@
+// Host driver of the whole search: the JADE loop of Sec. 2.1 (p = 1, fixed
+// F and CR) over every domain at once, the neighbour exchange of Sec. 3.4
+// after every exch_every-th selection, and the gradient polish. Everything
+// is enqueued on one stream; nothing synchronises. The selection of
+// generation g is fused into the step that mutates generation g+1 unless an
+// exchange must run between them.
+#include <utility>
+
+#include "tt_internal.cuh"
+
+tt::DeArgs tt_make_de_args(const tt_ctx* c, int gen);
+
+namespace {
+
+tt_status polish_impl(tt_ctx* c, const float* theta_in, float* theta_out, float* S_out,
+                      int steps, float lr, cudaStream_t s) {
+  const int n = c->n_dom, D = c->D;
+  if (n == 0) return TT_OK;
+  const float* lo = c->bounds;
+  const float* hi = c->bounds ? c->bounds + D : nullptr;
+  if (!lo) return tt_fail(c, TT_ERR_INVALID_ARG, "polish needs parameter bounds (a cfg)");
+  tt_status st = tt_cuda_check(
+      c, cudaMemcpyAsync(c->pol_th, theta_in, size_t(n) * D * 4, cudaMemcpyDeviceToDevice, s),
+      "polish copy");
+  if (st != TT_OK) return st;
+  for (int k = 0; k < steps; ++k) {
+    tt::EvalArgs a = c->eval_args(c->pol_th, 1, c->pol_S);
+    a.dS = c->pol_g;
+    st = tt_cuda_check(c, c->semblance(a, s, true), "polish gradient");
+    if (st != TT_OK) return st;
+    st = tt_cuda_check(c, c->counted(tt::launch_polish_update(n, D, c->pol_th, c->pol_g, c->pol_S,
+                                                   c->pol_bth, c->pol_bS, lo, hi, lr, k == 0, 0,
+                                                   s)),
+                       "polish update");
+    if (st != TT_OK) return st;
+  }
+  tt::EvalArgs a = c->eval_args(c->pol_th, 1, c->pol_S);
+  st = tt_cuda_check(c, c->semblance(a, s, false), "polish evaluation");
+  if (st != TT_OK) return st;
+  st = tt_cuda_check(c, c->counted(tt::launch_polish_update(n, D, c->pol_th, c->pol_g,
+                                                            c->pol_S, c->pol_bth, c->pol_bS, lo,
+                                                            hi, lr, steps == 0, 1, s)),
+                     "polish final");
+  if (st != TT_OK) return st;
+  st = tt_cuda_check(c, cudaMemcpyAsync(theta_out, c->pol_bth, size_t(n) * D * 4,
+                                        cudaMemcpyDeviceToDevice, s),
+                     "polish copy out");
+  if (st != TT_OK) return st;
+  if (S_out)
+    st = tt_cuda_check(c, cudaMemcpyAsync(S_out, c->pol_bS, size_t(n) * 4,
+                                          cudaMemcpyDeviceToDevice, s),
+                       "polish copy out");
+  return st;
+}
+
+}  // namespace
+
+extern "C" tt_status tt_polish(tt_ctx* c, float* theta, float* S, int32_t steps, float lr,
+                               void* stream) {
+  if (!c) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  if (steps < 0) return tt_fail(c, TT_ERR_INVALID_ARG, "steps < 0");
+  if (c->n_dom > 0 && !theta) return tt_fail(c, TT_ERR_INVALID_ARG, "theta is NULL");
+  return polish_impl(c, theta, theta, S, steps, lr, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" tt_status tt_search(tt_ctx* c, float* best_theta, float* best_S, uint64_t* n_evals,
+                               void* stream) {
+  if (!c) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->has_cfg) return tt_fail(c, TT_ERR_INVALID_ARG, "context was created without a cfg");
+  if (c->n_dom > 0 && (!best_theta || !best_S))
+    return tt_fail(c, TT_ERR_INVALID_ARG, "NULL output array");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const tt_de_cfg& cfg = c->cfg;
+  const int NP = cfg.np, NG = cfg.ng;
+  const bool grid = cfg.exch_every > 0 && c->n_m0 > 0 && c->n_t0 > 0 &&
+                    (long long)c->n_m0 * c->n_t0 == c->n_dom;
+  const unsigned long long edges =
+      grid ? 2ull * ((unsigned long long)c->n_m0 * (c->n_t0 - 1) +
+                     (unsigned long long)c->n_t0 * (c->n_m0 - 1))
+           : 0ull;
+  unsigned long long evals = 0;
+  tt_status st = TT_OK;
+#define STEP(expr, what)                                         \
+  do {                                                           \
+    st = tt_cuda_check(c, (expr), what);                         \
+    if (st != TT_OK) return st;                                  \
+  } while (0)
+  // generation 0: initialise and evaluate
+  tt::DeArgs a = tt_make_de_args(c, 0);
+  a.pop = c->pop;
+  a.fit = c->fit;
+  STEP(c->counted(tt::launch_de_step(a, s)), "init");
+  STEP(c->semblance(c->eval_args(c->pop, NP, c->fit), s, false), "evaluate init");
+  evals += (unsigned long long)NP * c->n_dom;
+  int cur = 0;            // trial buffer written by the next mutation
+  bool pending = false;   // trial[cur ^ 1] awaits selection
+  for (int g = 1; g <= NG; ++g) {
+    a = tt_make_de_args(c, g);
+    a.pop = c->pop;
+    a.fit = c->fit;
+    a.trial = pending ? c->trial[cur ^ 1] : nullptr;
+    a.tfit = pending ? c->tfit[cur ^ 1] : nullptr;
+    a.next = c->trial[cur];
+    STEP(c->counted(tt::launch_de_step(a, s)), "de step");
+    STEP(c->semblance(c->eval_args(c->trial[cur], NP, c->tfit[cur]), s, false), "evaluate");
+    evals += (unsigned long long)NP * c->n_dom;
+    pending = true;
+    cur ^= 1;
+    if (grid && g % cfg.exch_every == 0) {
+      a = tt_make_de_args(c, g);
+      a.pop = c->pop;
+      a.fit = c->fit;
+      a.trial = c->trial[cur ^ 1];
+      a.tfit = c->tfit[cur ^ 1];
+      STEP(c->counted(tt::launch_de_step(a, s)), "select");
+      pending = false;
+      STEP(c->counted(tt::launch_best_snapshot(c->n_dom, NP, c->D, c->pop, c->fit, c->snap,
+                                                nullptr, s)),
+           "snapshot");
+      STEP(c->counted(tt::launch_exchange_plan(c->n_m0, c->n_t0, NP, c->D, c->snap, c->pop,
+                                               c->fit, c->imports, c->slots, s)),
+           "exchange");
+      tt::EvalArgs ea = c->eval_args(c->imports, 4, c->fit);
+      ea.slots = c->slots;
+      ea.np_out = NP;
+      STEP(c->semblance(ea, s, false), "evaluate imports");
+      evals += edges;
+    }
+  }
+  if (pending) {
+    a = tt_make_de_args(c, NG + 1);
+    a.pop = c->pop;
+    a.fit = c->fit;
+    a.trial = c->trial[cur ^ 1];
+    a.tfit = c->tfit[cur ^ 1];
+    STEP(c->counted(tt::launch_de_step(a, s)), "final select");
+  }
+  STEP(c->counted(tt::launch_best_snapshot(c->n_dom, NP, c->D, c->pop, c->fit, best_theta,
+                                           best_S, s)),
+       "best");
+#undef STEP
+  if (cfg.polish_steps > 0) {
+    st = polish_impl(c, best_theta, best_theta, best_S, cfg.polish_steps, cfg.polish_lr, s);
+    if (st != TT_OK) return st;
+    evals += (unsigned long long)c->n_dom * (cfg.polish_steps + 1);
+  }
+  if (n_evals) *n_evals = evals;
+  return TT_OK;
+}

@@ -1,0 +1,289 @@
+// Semblance of a traveltime operator (K1) and its adjoint gradient (K2).
+//
+// Work decomposition: one thread per (domain, individual) pair, pairs laid
+// out domain-major so that a warp covers consecutive individuals of one
+// domain (P >= 32) or several consecutive domains of one group (P < 32).
+// Consecutive domains share a group (same m0, same aperture), so every lane
+// of a warp walks the same aperture entries in the same order: the
+// geometry-table loads are warp-uniform broadcasts and the 2w+2 samples that
+// each lane reads from a trace row sit at nearby addresses for nearby t0 and
+// for a converging population, which the L1 cache turns into reuse.
+//
+// Per aperture trace i (Sec. 2, the W_l x T_a inner loop of eq. order):
+//   U = (it0 + (A/dt) dm)^2 + (B/dt^2) dm^2 + (C/dt^2) h^2   (samples^2)
+//   u = min(sqrt(U), ns + w)  -- NaN from U < 0 also maps to ns + w, where
+//                                the whole window reads padding zeros
+//   j = floor(u), f = u - j, a_k = x[j+k] + f (x[j+k+1] - x[j+k])
+//   s_k += a_k, E += a_k^2
+// S = sum_k s_k^2 / (N E) (0 when E = 0).
+#include "tt_internal.cuh"
+
+namespace tt {
+namespace {
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <typename T>
+__device__ __forceinline__ float ld_sample(const T* p);
+template <>
+__device__ __forceinline__ float ld_sample<float>(const float* p) {
+  return __ldg(p);
+}
+template <>
+__device__ __forceinline__ float ld_sample<__nv_bfloat16>(const __nv_bfloat16* p) {
+  unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p));
+  return __uint_as_float(unsigned(u) << 16);
+}
+
+// Per-lane prologue shared by K1 and K2.
+struct Lane {
+  int d, p, e0, e1;
+  float p0, ca, cb, cc, inv_dt;
+};
+
+template <int OP>
+__device__ __forceinline__ bool lane_setup(const EvalArgs& a, long long q, Lane& L) {
+  if (q >= (long long)a.n_dom * a.P) return false;
+  L.d = int(q / a.P);
+  L.p = int(q - (long long)L.d * a.P);
+  int g = a.dom_group[L.d];
+  L.inv_dt = a.g_inv_dt[g];
+  L.e0 = a.ap_ptr[g];
+  L.e1 = a.ap_ptr[g + 1];
+  L.p0 = float(a.dom_it0[L.d]);
+  const float* th = a.theta + q * (OP == TT_OP_CMP ? 1 : 3);
+  float i2 = L.inv_dt * L.inv_dt;
+  if (OP == TT_OP_CMP) {
+    L.ca = 0.f;
+    L.cb = 0.f;
+    L.cc = th[0] * i2;
+  } else {
+    L.ca = th[0] * L.inv_dt;
+    L.cb = th[1] * i2;
+    L.cc = th[2] * i2;
+  }
+  return true;
+}
+
+template <int OP>
+__device__ __forceinline__ float position_sq(const Lane& L, float4 t4, float& qv) {
+  if (OP == TT_OP_CMP) {
+    qv = L.p0;
+    return fmaf(L.cc, t4.z, L.p0 * L.p0);
+  }
+  qv = fmaf(L.ca, t4.x, L.p0);
+  return fmaf(L.cb, t4.y, fmaf(L.cc, t4.z, qv * qv));
+}
+
+template <int OP, int W, typename T>
+__global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
+  constexpr int K = 2 * W + 1;
+  const long long q = (long long)blockIdx.x * kBlock + threadIdx.x;
+  Lane L;
+  if (!lane_setup<OP>(a, q, L)) return;
+  const T* __restrict__ tr = static_cast<const T*>(a.traces);
+  float s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = 0.f;
+  float E = 0.f;
+  for (int e = L.e0; e < L.e1; ++e) {
+    const float4 t4 = __ldg(a.ap_tab + e);
+    float qv;
+    const float U = position_sq<OP>(L, t4, qv);
+    const float u = fminf(sqrt_approx(U), a.umax);
+    const float fl = truncf(u);
+    const float f = u - fl;
+    const T* x = tr + (__float_as_uint(t4.w) + int(fl) - W);
+    float xv[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float ak = fmaf(f, xv[k + 1] - xv[k], xv[k]);
+      s[k] += ak;
+      E = fmaf(ak, ak, E);
+    }
+  }
+  float Q = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
+  const float N = float(L.e1 - L.e0);
+  const float S = (E > 0.f) ? Q / (N * E) : 0.f;
+  if (a.slots) {
+    const int slot = a.slots[q];
+    if (slot >= 0) a.S[(size_t)L.d * a.np_out + slot] = S;
+  } else {
+    a.S[q] = S;
+  }
+}
+
+// K2: two passes over the aperture. Pass 1 = K1 (s_k, E, S). With
+// alpha = 2/(N E), beta = 2 S / E, dS/da_ik = alpha s_k - beta a_ik, so pass 2
+// forms dS/du_i = sum_k (alpha s_k - beta a_ik)(x[j+k+1] - x[j+k]) and
+// chains it through du/dtheta:
+//   du/dA = (it0 + A dm/dt) dm / (u dt),  du/dB = dm^2 / (2 u dt^2),
+//   du/dC = h^2 / (2 u dt^2).
+template <int OP, int W, typename T>
+__global__ void __launch_bounds__(kBlock) k_semblance_grad(const EvalArgs a) {
+  constexpr int K = 2 * W + 1;
+  constexpr int D = OP == TT_OP_CMP ? 1 : 3;
+  const long long q = (long long)blockIdx.x * kBlock + threadIdx.x;
+  Lane L;
+  if (!lane_setup<OP>(a, q, L)) return;
+  const T* __restrict__ tr = static_cast<const T*>(a.traces);
+  float s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = 0.f;
+  float E = 0.f;
+  for (int e = L.e0; e < L.e1; ++e) {
+    const float4 t4 = __ldg(a.ap_tab + e);
+    float qv;
+    const float u = fminf(sqrt_approx(position_sq<OP>(L, t4, qv)), a.umax);
+    const float fl = truncf(u);
+    const float f = u - fl;
+    const T* x = tr + (__float_as_uint(t4.w) + int(fl) - W);
+    float xv[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float ak = fmaf(f, xv[k + 1] - xv[k], xv[k]);
+      s[k] += ak;
+      E = fmaf(ak, ak, E);
+    }
+  }
+  float Q = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
+  const float N = float(L.e1 - L.e0);
+  const float S = (E > 0.f) ? Q / (N * E) : 0.f;
+  float G0 = 0.f, G1 = 0.f, G2 = 0.f;
+  if (E > 0.f) {
+    const float alpha = 2.f / (N * E);
+    const float beta = 2.f * S / E;
+    for (int e = L.e0; e < L.e1; ++e) {
+      const float4 t4 = __ldg(a.ap_tab + e);
+      float qv;
+      const float u = fminf(sqrt_approx(position_sq<OP>(L, t4, qv)), a.umax);
+      const float fl = truncf(u);
+      const float f = u - fl;
+      const T* x = tr + (__float_as_uint(t4.w) + int(fl) - W);
+      float xv[K + 1];
+#pragma unroll
+      for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
+      float sg = 0.f, ag = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float gk = xv[k + 1] - xv[k];
+        const float ak = fmaf(f, gk, xv[k]);
+        sg = fmaf(s[k], gk, sg);
+        ag = fmaf(ak, gk, ag);
+      }
+      const float dSdu = fmaf(alpha, sg, -beta * ag);
+      const float inv_u = (u > 0.f && u < a.umax) ? 1.f / u : 0.f;
+      const float c = dSdu * inv_u;
+      if (OP == TT_OP_CRS) {
+        G0 = fmaf(c * qv, t4.x, G0);
+        G1 = fmaf(0.5f * c, t4.y, G1);
+      }
+      G2 = fmaf(0.5f * c, t4.z, G2);
+    }
+  }
+  a.S[q] = S;
+  float* out = a.dS + q * D;
+  const float i2 = L.inv_dt * L.inv_dt;
+  if (OP == TT_OP_CRS) {
+    out[0] = G0 * L.inv_dt;
+    out[1] = G1 * i2;
+    out[2] = G2 * i2;
+  } else {
+    out[0] = G2 * i2;
+  }
+}
+
+using KFn = void (*)(const EvalArgs);
+
+template <int OP, typename T>
+KFn pick_fwd(int W) {
+  switch (W) {
+    case 0: return k_semblance<OP, 0, T>;
+    case 1: return k_semblance<OP, 1, T>;
+    case 2: return k_semblance<OP, 2, T>;
+    case 3: return k_semblance<OP, 3, T>;
+    case 4: return k_semblance<OP, 4, T>;
+    case 5: return k_semblance<OP, 5, T>;
+    case 6: return k_semblance<OP, 6, T>;
+    case 7: return k_semblance<OP, 7, T>;
+    case 8: return k_semblance<OP, 8, T>;
+  }
+  return nullptr;
+}
+
+template <int OP, typename T>
+KFn pick_grad(int W) {
+  switch (W) {
+    case 0: return k_semblance_grad<OP, 0, T>;
+    case 1: return k_semblance_grad<OP, 1, T>;
+    case 2: return k_semblance_grad<OP, 2, T>;
+    case 3: return k_semblance_grad<OP, 3, T>;
+    case 4: return k_semblance_grad<OP, 4, T>;
+    case 5: return k_semblance_grad<OP, 5, T>;
+    case 6: return k_semblance_grad<OP, 6, T>;
+    case 7: return k_semblance_grad<OP, 7, T>;
+    case 8: return k_semblance_grad<OP, 8, T>;
+  }
+  return nullptr;
+}
+
+KFn select_kernel(const EvalArgs& a, bool grad) {
+  const bool bf = a.storage == TT_STORE_BF16;
+  if (a.op == TT_OP_CMP)
+    return grad ? (bf ? pick_grad<TT_OP_CMP, __nv_bfloat16>(a.W) : pick_grad<TT_OP_CMP, float>(a.W))
+                : (bf ? pick_fwd<TT_OP_CMP, __nv_bfloat16>(a.W) : pick_fwd<TT_OP_CMP, float>(a.W));
+  return grad ? (bf ? pick_grad<TT_OP_CRS, __nv_bfloat16>(a.W) : pick_grad<TT_OP_CRS, float>(a.W))
+              : (bf ? pick_fwd<TT_OP_CRS, __nv_bfloat16>(a.W) : pick_fwd<TT_OP_CRS, float>(a.W));
+}
+
+cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
+  const long long n = (long long)a.n_dom * a.P;
+  if (n == 0) return cudaSuccess;
+  KFn fn = select_kernel(a, grad);
+  if (!fn) return cudaErrorInvalidValue;
+  const long long blocks = (n + kBlock - 1) / kBlock;
+  if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+  fn<<<unsigned(blocks), kBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_semblance(const EvalArgs& a, cudaStream_t s) { return launch(a, s, false); }
+cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s) { return launch(a, s, true); }
+
+}  // namespace tt
+
+extern "C" tt_status tt_semblance_eval(tt_ctx* ctx, const float* theta, int32_t P, float* S,
+                                       void* stream) {
+  if (!ctx) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  if (P < 1) return tt_fail(ctx, TT_ERR_INVALID_ARG, "P must be >= 1");
+  if (ctx->n_dom > 0 && (!theta || !S)) return tt_fail(ctx, TT_ERR_INVALID_ARG, "NULL array");
+  tt::EvalArgs a = ctx->eval_args(theta, P, S);
+  return tt_cuda_check(ctx, ctx->semblance(a, static_cast<cudaStream_t>(stream), false),
+                       "semblance launch");
+}
+
+extern "C" tt_status tt_semblance_grad(tt_ctx* ctx, const float* theta, int32_t P, float* S,
+                                       float* dS, void* stream) {
+  if (!ctx) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  if (P < 1) return tt_fail(ctx, TT_ERR_INVALID_ARG, "P must be >= 1");
+  if (ctx->n_dom > 0 && (!theta || !S || !dS))
+    return tt_fail(ctx, TT_ERR_INVALID_ARG, "NULL array");
+  tt::EvalArgs a = ctx->eval_args(theta, P, S);
+  a.dS = dS;
+  return tt_cuda_check(ctx, ctx->semblance(a, static_cast<cudaStream_t>(stream), true),
+                       "semblance gradient launch");
+}

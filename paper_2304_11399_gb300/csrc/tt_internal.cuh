@@ -1,0 +1,116 @@
+// Internal declarations shared by the libtt translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tt.h"
+
+namespace tt {
+
+// Padded trace layout: sample n of trace r lives at r * pitch + kPadFront + n.
+// kPadFront >= max half window; kPadBack >= 2 * max half window + 2 so that a
+// window whose position is clamped to ns + w reads only padding zeros.
+constexpr int kPadFront = 8;
+constexpr int kPadBack = 24;
+constexpr int kBlock = 256;
+
+inline int padded_pitch(int ns) { return ((kPadFront + ns + kPadBack) + 15) / 16 * 16; }
+
+// Everything a semblance launch needs (passed by value to the kernels).
+struct EvalArgs {
+  const void* traces;       // padded traces, float or bf16
+  const float4* ap_tab;     // per aperture entry: dm, dm^2, h^2, row offset (bits)
+  const int* ap_ptr;        // [G+1]
+  const float* g_inv_dt;    // [G]
+  const int* dom_it0;       // [n_dom]
+  const int* dom_group;     // [n_dom]
+  int n_dom, P, D, op, W, storage;
+  float umax;               // ns + W: positions are clamped here (window all zero)
+  const float* theta;       // [n_dom][P][D]
+  float* S;                 // [n_dom][P], or fit [n_dom][np_out] in scatter mode
+  float* dS;                // [n_dom][P][D] (gradient launches)
+  const int* slots;         // scatter mode: result (d, p) -> S[d*np_out + slots[d*P+p]]
+  int np_out;
+};
+
+cudaError_t launch_semblance(const EvalArgs& a, cudaStream_t s);
+cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s);
+
+struct DeArgs {
+  int n_dom, NP, D, gen;
+  float* pop;
+  float* fit;
+  const float* trial;
+  const float* tfit;
+  float* next;
+  int* best_idx;
+  uint32_t key0, key1;
+  float F;
+  uint32_t cr_thr;          // floor(CR * 2^24)
+  float lo[TT_MAX_DIM], hi[TT_MAX_DIM];
+};
+
+cudaError_t launch_de_step(const DeArgs& a, cudaStream_t s);
+cudaError_t launch_best_snapshot(int n_dom, int NP, int D, const float* pop, const float* fit,
+                                 float* best_theta, float* best_S, cudaStream_t s);
+cudaError_t launch_exchange_plan(int n_m0, int n_t0, int NP, int D, const float* best_theta,
+                                 float* pop, const float* fit, float* imports, int* slots,
+                                 cudaStream_t s);
+cudaError_t launch_polish_update(int n_dom, int D, float* th, const float* g, const float* S,
+                                 float* best_th, float* best_S, const float* lo, const float* hi,
+                                 float lr, int first, int last, cudaStream_t s);
+
+}  // namespace tt
+
+struct tt_ctx {
+  int device = 0;
+  // gathers (padded device copy)
+  int n_traces = 0, ns = 0, storage = TT_STORE_F32, pitch = 0;
+  void* traces = nullptr;
+  float* mid = nullptr;     // copies kept to rebuild nothing; used by reloads
+  float* off = nullptr;
+  float* stage = nullptr;   // f32 staging rows for bf16 reloads (n_traces*ns), lazily
+  // problem
+  int op = 0, W = 0, D = 1, n_groups = 0, n_dom = 0, n_m0 = 0, n_t0 = 0;
+  long long nnz = 0;
+  float* g_inv_dt = nullptr;
+  int* ap_ptr = nullptr;
+  float4* ap_tab = nullptr;
+  int* dom_it0 = nullptr;
+  int* dom_group = nullptr;
+  // search settings and scratch
+  bool has_cfg = false;
+  tt_de_cfg cfg{};
+  float* bounds = nullptr;  // [2][D] lo, hi on the device
+  float *pop = nullptr, *fit = nullptr, *trial[2] = {nullptr, nullptr};
+  float* tfit[2] = {nullptr, nullptr};
+  float *snap = nullptr, *imports = nullptr;
+  int *slots = nullptr, *best_idx = nullptr;
+  float *pol_th = nullptr, *pol_g = nullptr, *pol_S = nullptr, *pol_bth = nullptr,
+        *pol_bS = nullptr;
+  int* d_err = nullptr;     // device-side validation flag
+  std::string err;
+  // counters and optional event timing of semblance launches
+  double sum_N = 0;         // sum over domains of the aperture size
+  unsigned long long n_launch = 0, n_sem = 0, n_timed = 0;
+  double trace_evals = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;   // pairs (start, end)
+  size_t ev_used = 0;
+
+  tt::EvalArgs eval_args(const float* theta, int P, float* S) const;
+  // every semblance / gradient launch of the library goes through here
+  cudaError_t semblance(const tt::EvalArgs& a, cudaStream_t s, bool grad);
+  cudaError_t counted(cudaError_t e) {
+    ++n_launch;
+    return e;
+  }
+};
+
+tt_status tt_fail(tt_ctx* ctx, tt_status code, const char* fmt, ...);
+tt_status tt_cuda_check(tt_ctx* ctx, cudaError_t e, const char* what);
