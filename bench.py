@@ -40,8 +40,9 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 def workload_config(wl, n_gpus):
     p = wl.problem
+    sub = "" if p.n_m0 in (0, 200) else f" (first {p.n_m0} CMPs solved)"
     return {"workload": "CRS line 200 CMP x 48 offsets x 1500 samples (dt 4 ms), "
-                        "aperture +-10 CMP, window 11",
+                        "aperture +-10 CMP, window 11" + sub,
             "n_dom": p.n_dom, "np": wl.de.np, "ng": wl.de.ng, "exch_every": wl.de.exch_every,
             "polish_steps": wl.de.polish_steps, "storage": wl.storage,
             "l2": "flushed between timed steps (256 MiB write)",
@@ -150,6 +151,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--cmps", type=int, default=0,
+                    help="solve only the first CMPS midpoints of the line (profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -172,6 +175,10 @@ def main():
 
     wl = configs.crs_line(rank)
     wl.storage = args.storage
+    if args.cmps:
+        import synth
+        wl.problem = synth.line_problem(wl.line, half_window=5, ap_half=10,
+                                        cmps=list(range(args.cmps)))
     prob = wl.problem
     # CPU baseline first (rank 0, N = 1): the oracle as it stands on a sample
     cpu = None

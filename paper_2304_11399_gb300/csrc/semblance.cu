@@ -79,12 +79,10 @@ __device__ __forceinline__ float position_sq(const Lane& L, float4 t4, float& qv
   return fmaf(L.cb, t4.y, fmaf(L.cc, t4.z, qv * qv));
 }
 
+// Scalar evaluation of one (domain, individual) pair over its aperture.
 template <int OP, int W, typename T>
-__global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
+__device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
   constexpr int K = 2 * W + 1;
-  const long long q = (long long)blockIdx.x * kBlock + threadIdx.x;
-  Lane L;
-  if (!lane_setup<OP>(a, q, L)) return;
   const T* __restrict__ tr = static_cast<const T*>(a.traces);
   float s[K];
 #pragma unroll
@@ -112,13 +110,83 @@ __global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
 #pragma unroll
   for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
   const float N = float(L.e1 - L.e0);
-  const float S = (E > 0.f) ? Q / (N * E) : 0.f;
+  return (E > 0.f) ? Q / (N * E) : 0.f;
+}
+
+__device__ __forceinline__ void store_S(const EvalArgs& a, long long q, int d, float S) {
   if (a.slots) {
     const int slot = a.slots[q];
-    if (slot >= 0) a.S[(size_t)L.d * a.np_out + slot] = S;
+    if (slot >= 0) a.S[(size_t)d * a.np_out + slot] = S;
   } else {
     a.S[q] = S;
   }
+}
+
+// K1. Each thread evaluates two (domain, individual) pairs, q and q + 32 of
+// its warp's 64 consecutive pairs. When both lie in one group (the common
+// case: same aperture, possibly different t0) the aperture is walked once
+// and the two windows are processed with packed FP32x2 arithmetic: sample
+// k of the two pairs forms one register pair, so every interpolation,
+// stack and energy update is one f32x2 instruction for both. Otherwise
+// (a group boundary inside the warp, or no second pair) each pair is
+// evaluated on its own.
+template <int OP, int W, typename T>
+__global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
+  constexpr int K = 2 * W + 1;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const long long q0 = warp * 64 + lane, q1 = q0 + 32;
+  Lane L0, L1;
+  const bool v0 = lane_setup<OP>(a, q0, L0);
+  if (!v0) return;
+  const bool v1 = lane_setup<OP>(a, q1, L1);
+  if (!v1 || L1.e0 != L0.e0 || L1.e1 != L0.e1 || L1.inv_dt != L0.inv_dt) {
+    store_S(a, q0, L0.d, eval_scalar<OP, W, T>(a, L0));
+    if (v1) store_S(a, q1, L1.d, eval_scalar<OP, W, T>(a, L1));
+    return;
+  }
+  const T* __restrict__ tr = static_cast<const T*>(a.traces);
+  const float2 ca = make_float2(L0.ca, L1.ca), cb = make_float2(L0.cb, L1.cb),
+               cc = make_float2(L0.cc, L1.cc), p0 = make_float2(L0.p0, L1.p0);
+  const float2 p0sq = __fmul2_rn(p0, p0);
+  float2 s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = make_float2(0.f, 0.f);
+  float2 E = make_float2(0.f, 0.f);
+  for (int e = L0.e0; e < L0.e1; ++e) {
+    const float4 t4 = __ldg(a.ap_tab + e);
+    float2 U;
+    if (OP == TT_OP_CMP) {
+      U = __ffma2_rn(cc, make_float2(t4.z, t4.z), p0sq);
+    } else {
+      const float2 qv = __ffma2_rn(ca, make_float2(t4.x, t4.x), p0);
+      U = __ffma2_rn(cc, make_float2(t4.z, t4.z), __fmul2_rn(qv, qv));
+      U = __ffma2_rn(cb, make_float2(t4.y, t4.y), U);
+    }
+    const float u0 = fminf(sqrt_approx(U.x), a.umax);
+    const float u1 = fminf(sqrt_approx(U.y), a.umax);
+    const float fl0 = truncf(u0), fl1 = truncf(u1);
+    const float2 f = make_float2(u0 - fl0, u1 - fl1);
+    const float2 g = make_float2(1.f - f.x, 1.f - f.y);
+    const unsigned base = __float_as_uint(t4.w) - W;
+    const T* x0 = tr + (base + int(fl0));
+    const T* x1 = tr + (base + int(fl1));
+    float2 xv[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) xv[k] = make_float2(ld_sample<T>(x0 + k), ld_sample<T>(x1 + k));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 ak = __ffma2_rn(f, xv[k + 1], __fmul2_rn(g, xv[k]));
+      s[k] = __fadd2_rn(s[k], ak);
+      E = __ffma2_rn(ak, ak, E);
+    }
+  }
+  float2 Q = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < K; ++k) Q = __ffma2_rn(s[k], s[k], Q);
+  const float N = float(L0.e1 - L0.e0);
+  store_S(a, q0, L0.d, (E.x > 0.f) ? Q.x / (N * E.x) : 0.f);
+  store_S(a, q1, L1.d, (E.y > 0.f) ? Q.y / (N * E.y) : 0.f);
 }
 
 // K2: two passes over the aperture. Pass 1 = K1 (s_k, E, S). With
@@ -253,7 +321,8 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
   if (n == 0) return cudaSuccess;
   KFn fn = select_kernel(a, grad);
   if (!fn) return cudaErrorInvalidValue;
-  const long long blocks = (n + kBlock - 1) / kBlock;
+  const long long per_block = grad ? kBlock : 2ll * kBlock;  // K1: two pairs per thread
+  const long long blocks = (n + per_block - 1) / per_block;
   if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
   fn<<<unsigned(blocks), kBlock, 0, s>>>(a);
   return cudaGetLastError();

@@ -58,7 +58,7 @@ def test_grad_matches_central_differences(points):
     lo, hi = np.array(configs.CRS_LO), np.array(configs.CRS_HI)
     n = prob.n_dom
     h = 1e-4 * np.maximum(np.abs(theta[:, 0, :]), hi - lo)
-    checked = 0
+    checked = checked32 = 0
     for k in range(3):
         tp, tm = theta.copy(), theta.copy()
         tp[:, 0, k] += h[:, k].astype(np.float32)
@@ -72,6 +72,10 @@ def test_grad_matches_central_differences(points):
         fd32 = (Sp_g.astype(np.float64) - Sm_g) / (2 * hk)
         scale = np.median(np.abs(fd64)) + 1e-30
         for d in range(n):
+            u0, T0 = _positions(wl, prob, theta[d, 0], d)
+            fr = u0 - np.floor(u0)
+            if np.any((T0 > 0) & ((fr < 1e-3) | (fr > 1 - 1e-3))):
+                continue  # a trace at a kink: FP32 and FP64 may take opposite sides
             up, Tp = _positions(wl, prob, tp[d, 0], d)
             um, Tm = _positions(wl, prob, tm[d, 0], d)
             if np.any(np.floor(up) != np.floor(um)) or np.any((Tp > 0) != (Tm > 0)):
@@ -79,10 +83,13 @@ def test_grad_matches_central_differences(points):
             checked += 1
             assert abs(G[d, k] - fd64[d]) <= 2e-2 * (abs(fd64[d]) + scale), (k, d)
             # the FP32 difference quotient carries the rounding of two FP32
-            # semblance values (|dS| <= 2e-7 each) divided by 2h
-            noise = 4e-7 / (2 * hk[d])
-            assert abs(G[d, k] - fd32[d]) <= 5e-2 * (abs(fd64[d]) + scale) + noise, (k, d)
-    assert checked >= 600
+            # semblance values (observed up to ~1e-6 each) divided by 2h, so it
+            # is checked only where the change of S resolves the gradient
+            if abs(fd64[d]) * 2 * hk[d] >= 2e-5:
+                noise = 2e-6 / (2 * hk[d])
+                assert abs(G[d, k] - fd32[d]) <= 5e-2 * (abs(fd64[d]) + scale) + noise, (k, d)
+                checked32 += 1
+    assert checked >= 600 and checked32 >= 300
 
 
 def test_autograd_backward_is_adjoint(points):
@@ -93,7 +100,7 @@ def test_autograd_backward_is_adjoint(points):
     (out * w).sum().backward()
     expect = w.unsqueeze(-1) * to_dev(G).unsqueeze(1)
     torch.testing.assert_close(th.grad, expect, rtol=1e-6, atol=0)
-    torch.testing.assert_close(out.detach().cpu().numpy()[:, 0], S, rtol=0, atol=1e-7)
+    np.testing.assert_allclose(out.detach().cpu().numpy()[:, 0], S, rtol=0, atol=1e-7)
 
 
 def test_cmp_gradient_and_polish():
