@@ -226,6 +226,32 @@ tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
 tt_status tt_search(tt_ctx* ctx, float* best_theta, float* best_S, uint64_t* n_evals,
                     void* stream);
 
+/* Allocation-free semblance evaluation. The paper has no counterpart: this
+ * entry point serves callers that cannot allocate device memory, such as a
+ * plug-in whose host application owns every device buffer, or a service loop
+ * in which cudaMalloc (which may synchronise the device and can fail once
+ * memory is fragmented) is not allowed after start-up. Such callers cannot
+ * create a context, so this call evaluates exactly what tt_semblance_eval
+ * evaluates, directly on the caller's arrays: gathers (storage must be
+ * TT_STORE_F32; the traces are read in place), problem, theta
+ * [n_dom][P][D] and S [n_dom][P], all device pointers owned by the caller.
+ * It calls no cudaMalloc or cudaFree. Its scratch (the aperture geometry
+ * table and a validation flag) is a fixed device array of
+ * TT_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
+ * the library until the process exits; problems whose aperture lists hold
+ * more than TT_NOALLOC_MAX_APERTURE_ENTRIES entries are rejected with
+ * TT_ERR_UNSUPPORTED. The first call on a device (with that device current)
+ * looks up the array's device address; make it before any stream capture.
+ * Every call synchronises `stream` once, to read ap_ptr and the result of the
+ * on-device validation (INVALID_ARG as for tt_ctx_create), then enqueues the
+ * evaluation without waiting. All calls share the scratch array, which keeps
+ * the last call's contents: calls that overlap on the GPU race on it, so
+ * serialise them (one stream, or events). Error messages: tt_last_error(NULL). */
+#define TT_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define TT_NOALLOC_MAX_APERTURE_ENTRIES 262128
+tt_status tt_semblance_eval_noalloc(const tt_gathers* gathers, const tt_problem* problem,
+                                    const float* theta, int32_t P, float* S, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,8 @@ TT_OK, TT_ERR_INVALID_ARG, TT_ERR_CUDA, TT_ERR_OUT_OF_MEMORY, TT_ERR_TIMEOUT, \
 TT_OP_CMP, TT_OP_CRS = 0, 1
 TT_STORE_F32, TT_STORE_BF16 = 0, 1
 TT_MAX_DIM = 8
+TT_NOALLOC_SCRATCH_BYTES = 4 << 20
+TT_NOALLOC_MAX_APERTURE_ENTRIES = 262128
 
 STATUS_NAMES = {0: "TT_OK", 1: "TT_ERR_INVALID_ARG", 2: "TT_ERR_CUDA",
                 3: "TT_ERR_OUT_OF_MEMORY", 4: "TT_ERR_TIMEOUT", 5: "TT_ERR_UNSUPPORTED"}
@@ -61,6 +63,7 @@ SIGNATURES = {
     "tt_search": (I32, [P, P, P, C.POINTER(C.c_uint64), P]),
     "tt_ctx_profile": (I32, [P, I32]),
     "tt_ctx_stats": (I32, [P, C.POINTER(Stats), I32]),
+    "tt_semblance_eval_noalloc": (I32, [C.POINTER(Gathers), C.POINTER(ProblemT), P, I32, P, P]),
 }
 
 _lib = None

@@ -1,0 +1,106 @@
+"""The allocation-free entry point, tt_semblance_eval_noalloc, through the C ABI.
+
+It serves callers that cannot allocate device memory (their host
+application owns every device buffer, or cudaMalloc is not allowed once
+their service loop runs) and therefore cannot create a context. It must
+give what tt_semblance_eval gives on the same inputs, within the FP32
+parity tolerance of the other tests (|dS| <= 1e-5), also when two calls
+follow each other and share the library's fixed scratch array. This file is
+collected last so that a run stopping at its first failure has run
+everything else first; it also passes on its own in a fresh process.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2304_11399_gb300 as tt
+from paper_2304_11399_gb300 import _lib
+from gpu_util import dev, random_theta, to_dev, small_line, configs, synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _cabi_args(traces, mid, off, prob):
+    """Device copies of the inputs and the tt_gathers / tt_problem structs."""
+    keep = dict(traces=to_dev(traces), mid=to_dev(mid), off=to_dev(off),
+                group_m0=to_dev(prob.group_m0), group_dt=to_dev(prob.group_dt),
+                ap_ptr=to_dev(prob.ap_ptr, torch.int32), ap_idx=to_dev(prob.ap_idx, torch.int32),
+                dom_it0=to_dev(prob.dom_it0, torch.int32),
+                dom_group=to_dev(prob.dom_group, torch.int32))
+    g = _lib.Gathers(int(traces.shape[0]), int(traces.shape[1]), _lib.TT_STORE_F32, 0,
+                     keep["traces"].data_ptr(), keep["mid"].data_ptr(), keep["off"].data_ptr())
+    p = _lib.ProblemT(int(prob.op), int(prob.half_window), int(prob.group_m0.size),
+                      int(prob.dom_it0.size),
+                      *(keep[k].data_ptr() for k in ("group_m0", "group_dt", "ap_ptr", "ap_idx",
+                                                    "dom_it0", "dom_group")), 0, 0)
+    return g, p, keep
+
+
+def _noalloc(lib, g, p, theta_t, S_t):
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return lib.tt_semblance_eval_noalloc(C.byref(g), C.byref(p), C.c_void_p(theta_t.data_ptr()),
+                                         int(theta_t.shape[1]), C.c_void_p(S_t.data_ptr()),
+                                         stream)
+
+
+def _context_eval(traces, mid, off, prob, theta):
+    ctx = tt.tt_ctx_create(traces, mid, off, prob, None, device=dev())
+    S = tt.tt_semblance_eval(ctx, to_dev(theta)).cpu().numpy()
+    ctx.close()
+    return S
+
+
+def test_noalloc_matches_context_path_on_two_calls_in_a_row():
+    lib = _lib.load()
+    # call 1: a CRS line (uneven apertures clipped at the line ends, P = 20)
+    wa = small_line(21)
+    ta = random_theta(wa.problem.n_dom, 20, wa.de.lo, wa.de.hi, 1)
+    # call 2: the CMP gather, every sample, P = 7 (rewrites the shared scratch)
+    wb = configs.cmp_search(2)
+    tb = random_theta(wb.problem.n_dom, 7, wb.de.lo, wb.de.hi, 2)
+    ga, pa, ka = _cabi_args(wa.traces, wa.mid, wa.off, wa.problem)
+    gb, pb, kb = _cabi_args(wb.traces, wb.mid, wb.off, wb.problem)
+    ta_t, tb_t = to_dev(ta), to_dev(tb)
+    Sa = torch.full((wa.problem.n_dom, 20), -1.0, device=dev())
+    Sb = torch.full((wb.problem.n_dom, 7), -1.0, device=dev())
+    assert _noalloc(lib, ga, pa, ta_t, Sa) == _lib.TT_OK, lib.tt_last_error(None)
+    assert _noalloc(lib, gb, pb, tb_t, Sb) == _lib.TT_OK, lib.tt_last_error(None)
+    torch.cuda.synchronize()
+    ref_a = _context_eval(wa.traces, wa.mid, wa.off, wa.problem, ta)
+    ref_b = _context_eval(wb.traces, wb.mid, wb.off, wb.problem, tb)
+    assert np.max(np.abs(Sa.cpu().numpy() - ref_a)) <= TOL
+    assert np.max(np.abs(Sb.cpu().numpy() - ref_b)) <= TOL
+    # the same call again after the other one: same answer as the first time
+    Sa2 = torch.full_like(Sa, -1.0)
+    assert _noalloc(lib, ga, pa, ta_t, Sa2) == _lib.TT_OK
+    torch.cuda.synchronize()
+    assert torch.equal(Sa, Sa2)
+
+
+def test_noalloc_rejects_oversize_and_invalid_input():
+    lib = _lib.load()
+    wl = small_line(22, n_cmp=3, ns=60, ap_half=1)
+    prob = wl.problem
+    # an aperture list one entry longer than the fixed scratch holds
+    n_big = _lib.TT_NOALLOC_MAX_APERTURE_ENTRIES + 1
+    big = synth.Problem(op=1, half_window=5, group_m0=np.zeros(1, np.float32),
+                        group_dt=np.full(1, 0.004, np.float32),
+                        ap_ptr=np.array([0, n_big], np.int32), ap_idx=np.zeros(n_big, np.int32),
+                        dom_it0=np.zeros(1, np.int32), dom_group=np.zeros(1, np.int32))
+    g, p, keep = _cabi_args(wl.traces, wl.mid, wl.off, big)
+    th = torch.zeros((1, 1, 3), device=dev())
+    S = torch.zeros((1, 1), device=dev())
+    assert _noalloc(lib, g, p, th, S) == _lib.TT_ERR_UNSUPPORTED
+    assert b"at most" in lib.tt_last_error(None)
+    # an out-of-range trace index is caught on the device and reported
+    bad = synth.Problem(**{**prob.__dict__})
+    bad.ap_idx = prob.ap_idx.copy()
+    bad.ap_idx[5] = wl.traces.shape[0]
+    g, p, keep = _cabi_args(wl.traces, wl.mid, wl.off, bad)
+    th = to_dev(random_theta(prob.n_dom, 2, wl.de.lo, wl.de.hi, 3))
+    S = torch.zeros((prob.n_dom, 2), device=dev())
+    assert _noalloc(lib, g, p, th, S) == _lib.TT_ERR_INVALID_ARG
+    assert b"ap_idx" in lib.tt_last_error(None)
