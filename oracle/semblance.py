@@ -68,7 +68,7 @@ def semblance_from_amplitudes(a: np.ndarray):
     s = np.sum(a, axis=-2)
     Q = np.sum(s * s, axis=-1)
     safe = np.where(E > 0.0, E, 1.0)
-    S = np.where((E > 0.0) & (N > 0), Q / (N * safe), 0.0)
+    S = np.where((E > 0.0) & (N > 0), Q / (max(N, 1) * safe), 0.0)
     return float(S) if S.ndim == 0 else S
 
 

@@ -73,10 +73,32 @@ template <int OP>
 __device__ __forceinline__ float position_sq(const Lane& L, float4 t4, float& qv) {
   if (OP == TT_OP_CMP) {
     qv = L.p0;
-    return fmaf(L.cc, t4.z, L.p0 * L.p0);
+    return fmaf(L.cc, t4.z, __fmul_rn(L.p0, L.p0));
   }
   qv = fmaf(L.ca, t4.x, L.p0);
-  return fmaf(L.cb, t4.y, fmaf(L.cc, t4.z, qv * qv));
+  return fmaf(L.cb, t4.y, fmaf(L.cc, t4.z, __fmul_rn(qv, qv)));
+}
+
+// Final normalisation S = Q / (N E). FP32-stored traces: E is one FP32
+// sum over the aperture. BF16-stored traces (long apertures, reduced-
+// precision data): E is accumulated in FP32 within chunks of 32 aperture
+// traces and the chunk sums are added in FP64, so the energy's rounding
+// error stays that of a 32-trace FP32 sum; the division is done in FP64.
+template <typename T>
+struct Chunk {
+  static constexpr bool kF64 = false;
+  static constexpr int kTraces = 1 << 30;  // one chunk: the whole aperture
+};
+template <>
+struct Chunk<__nv_bfloat16> {
+  static constexpr bool kF64 = true;
+  static constexpr int kTraces = 32;
+};
+
+template <typename T>
+__device__ __forceinline__ float normalise(float Q, int N, float E, double Ed) {
+  if (Chunk<T>::kF64) return (Ed > 0.0) ? float(double(Q) / (double(N) * Ed)) : 0.f;
+  return (E > 0.f) ? Q / (float(N) * E) : 0.f;
 }
 
 // Scalar evaluation of one (domain, individual) pair over its aperture.
@@ -87,30 +109,37 @@ __device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
   float s[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) s[k] = 0.f;
+  double Ed = 0.0;  // FP64 sum of per-chunk energies (BF16 storage only)
   float E = 0.f;
-  for (int e = L.e0; e < L.e1; ++e) {
-    const float4 t4 = __ldg(a.ap_tab + e);
-    float qv;
-    const float U = position_sq<OP>(L, t4, qv);
-    const float u = fminf(sqrt_approx(U), a.umax);
-    const float fl = truncf(u);
-    const float f = u - fl;
-    const T* x = tr + (__float_as_uint(t4.w) + int(fl) - W);
-    float xv[K + 1];
+  for (int c0 = L.e0, c1; c0 < L.e1; c0 = c1) {
+    c1 = (L.e1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : L.e1;
+    float Ec = 0.f;
+    for (int e = c0; e < c1; ++e) {
+      const float4 t4 = __ldg(a.ap_tab + e);
+      float qv;
+      const float U = position_sq<OP>(L, t4, qv);
+      const float u = fminf(sqrt_approx(U), a.umax);
+      const float fl = truncf(u);
+      const float f = u - fl, g = 1.f - f;
+      const T* x = tr + (__float_as_uint(t4.w) + int(fl) - W);
+      float xv[K + 1];
 #pragma unroll
-    for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
+      for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float ak = fmaf(f, xv[k + 1] - xv[k], xv[k]);
-      s[k] += ak;
-      E = fmaf(ak, ak, E);
+      for (int k = 0; k < K; ++k) {
+        // same operations, in the same order, as one lane of the packed path
+        const float ak = fmaf(f, xv[k + 1], __fmul_rn(g, xv[k]));
+        s[k] = __fadd_rn(s[k], ak);
+        Ec = fmaf(ak, ak, Ec);
+      }
     }
+    if (Chunk<T>::kF64) Ed += double(Ec); else E = Ec;
   }
   float Q = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
-  const float N = float(L.e1 - L.e0);
-  return (E > 0.f) ? Q / (N * E) : 0.f;
+  const int N = L.e1 - L.e0;
+  return normalise<T>(Q, N, E, Ed);
 }
 
 __device__ __forceinline__ void store_S(const EvalArgs& a, long long q, int d, float S) {
@@ -153,7 +182,11 @@ __global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
 #pragma unroll
   for (int k = 0; k < K; ++k) s[k] = make_float2(0.f, 0.f);
   float2 E = make_float2(0.f, 0.f);
-  for (int e = L0.e0; e < L0.e1; ++e) {
+  double Ed0 = 0.0, Ed1 = 0.0;  // FP64 chunk sums (BF16 storage only)
+  for (int c0 = L0.e0, c1; c0 < L0.e1; c0 = c1) {
+  c1 = (L0.e1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : L0.e1;
+  float2 Ec = make_float2(0.f, 0.f);
+  for (int e = c0; e < c1; ++e) {
     const float4 t4 = __ldg(a.ap_tab + e);
     float2 U;
     if (OP == TT_OP_CMP) {
@@ -178,15 +211,22 @@ __global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
     for (int k = 0; k < K; ++k) {
       const float2 ak = __ffma2_rn(f, xv[k + 1], __fmul2_rn(g, xv[k]));
       s[k] = __fadd2_rn(s[k], ak);
-      E = __ffma2_rn(ak, ak, E);
+      Ec = __ffma2_rn(ak, ak, Ec);
     }
+  }
+  if (Chunk<T>::kF64) {
+    Ed0 += double(Ec.x);
+    Ed1 += double(Ec.y);
+  } else {
+    E = Ec;
+  }
   }
   float2 Q = make_float2(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < K; ++k) Q = __ffma2_rn(s[k], s[k], Q);
-  const float N = float(L0.e1 - L0.e0);
-  store_S(a, q0, L0.d, (E.x > 0.f) ? Q.x / (N * E.x) : 0.f);
-  store_S(a, q1, L1.d, (E.y > 0.f) ? Q.y / (N * E.y) : 0.f);
+  const int N = L0.e1 - L0.e0;
+  store_S(a, q0, L0.d, normalise<T>(Q.x, N, E.x, Ed0));
+  store_S(a, q1, L1.d, normalise<T>(Q.y, N, E.y, Ed1));
 }
 
 // K2: two passes over the aperture. Pass 1 = K1 (s_k, E, S). With
