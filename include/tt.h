@@ -216,6 +216,37 @@ tt_status tt_ctx_profile(tt_ctx* ctx, int32_t enable);
  * launches are pending this waits for the last recorded event. */
 tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
 
+/* Launch options of a context (tt_ctx_set_option / tt_ctx_get_option):
+ *  TT_OPT_KERNEL  semblance kernel variant for forward evaluations:
+ *                 TT_KERNEL_PACKED (default; two parameter vectors per thread
+ *                 with packed FP32x2 arithmetic, one launch covering every
+ *                 (domain, vector) pair), TT_KERNEL_PERSISTENT (the same work
+ *                 in a persistent grid sized to the GPU, warps taking 64-pair
+ *                 work units from an atomic counter -- load balance for
+ *                 uneven apertures), TT_KERNEL_SCALAR (one pair per thread).
+ *                 All variants perform the same operations in the same order
+ *                 and give bit-identical S.
+ *  TT_OPT_BLOCK   threads per block, 128 or 256 (default 256).
+ *  TT_OPT_SEARCH_GRAPH  1 (default): tt_search captures its whole launch
+ *                 sequence into a CUDA graph on first use and replays it;
+ *                 0: launch eagerly. Searches run eagerly while profiling is
+ *                 enabled. Changing an option drops a captured graph. */
+enum { TT_OPT_KERNEL = 1, TT_OPT_BLOCK = 2, TT_OPT_SEARCH_GRAPH = 3 };
+enum { TT_KERNEL_PACKED = 1, TT_KERNEL_PERSISTENT = 2, TT_KERNEL_SCALAR = 3 };
+#define TT_N_TUNE_CANDIDATES 6
+tt_status tt_ctx_set_option(tt_ctx* ctx, int32_t option, int64_t value);
+tt_status tt_ctx_get_option(const tt_ctx* ctx, int32_t option, int64_t* value);
+
+/* Autotuner: times every (kernel variant, block size) candidate -- in the
+ * order packed/256, packed/128, persistent/256, persistent/128, scalar/256,
+ * scalar/128 -- on one evaluation of theta [n_dom][P][D] (S [n_dom][P]
+ * receives it), keeps the fastest as the context's TT_OPT_KERNEL and
+ * TT_OPT_BLOCK, and writes the mean time of each candidate in ms to
+ * times_ms (host, TT_N_TUNE_CANDIDATES entries, may be NULL). Synchronises
+ * `stream`. */
+tt_status tt_ctx_autotune(tt_ctx* ctx, const float* theta, int32_t P, float* S,
+                          float* times_ms, void* stream);
+
 /* The whole search (JADE loop of Sec. 2.1 with the exchange of Sec. 3.4):
  * init, NG generations of select/mutate/evaluate, an exchange after every
  * exch_every-th selection, then cfg polish_steps of polishing. Writes

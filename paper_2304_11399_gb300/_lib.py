@@ -10,6 +10,11 @@ LIB_PATH = os.path.join(PKG, "libtt.so")
 TT_OK, TT_ERR_INVALID_ARG, TT_ERR_CUDA, TT_ERR_OUT_OF_MEMORY, TT_ERR_TIMEOUT, \
     TT_ERR_UNSUPPORTED = range(6)
 TT_OP_CMP, TT_OP_CRS = 0, 1
+TT_OPT_KERNEL, TT_OPT_BLOCK, TT_OPT_SEARCH_GRAPH = 1, 2, 3
+TT_KERNEL_PACKED, TT_KERNEL_PERSISTENT, TT_KERNEL_SCALAR = 1, 2, 3
+TT_N_TUNE_CANDIDATES = 6
+TUNE_CANDIDATES = [("packed", 256), ("packed", 128), ("persistent", 256), ("persistent", 128),
+                   ("scalar", 256), ("scalar", 128)]
 TT_STORE_F32, TT_STORE_BF16 = 0, 1
 TT_MAX_DIM = 8
 TT_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -64,6 +69,9 @@ SIGNATURES = {
     "tt_ctx_profile": (I32, [P, I32]),
     "tt_ctx_stats": (I32, [P, C.POINTER(Stats), I32]),
     "tt_semblance_eval_noalloc": (I32, [C.POINTER(Gathers), C.POINTER(ProblemT), P, I32, P, P]),
+    "tt_ctx_set_option": (I32, [P, I32, C.c_int64]),
+    "tt_ctx_get_option": (I32, [P, I32, C.POINTER(C.c_int64)]),
+    "tt_ctx_autotune": (I32, [P, P, I32, P, C.POINTER(C.c_float), P]),
 }
 
 _lib = None

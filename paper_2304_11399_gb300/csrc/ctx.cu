@@ -56,7 +56,97 @@ tt::EvalArgs tt_ctx::eval_args(const float* theta, int P, float* S) const {
   a.dS = nullptr;
   a.slots = nullptr;
   a.np_out = 0;
+  a.kernel = kernel;
+  a.block = block;
+  a.queue = queue;
   return a;
+}
+
+void tt_ctx_drop_graph(tt_ctx* c) {
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+}
+
+extern "C" tt_status tt_ctx_set_option(tt_ctx* c, int32_t option, int64_t value) {
+  if (!c) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  switch (option) {
+    case TT_OPT_KERNEL:
+      if (value != TT_KERNEL_PACKED && value != TT_KERNEL_PERSISTENT && value != TT_KERNEL_SCALAR)
+        return tt_fail(c, TT_ERR_INVALID_ARG, "unknown kernel variant %lld", (long long)value);
+      c->kernel = int(value);
+      break;
+    case TT_OPT_BLOCK:
+      if (value != 128 && value != 256)
+        return tt_fail(c, TT_ERR_INVALID_ARG, "block must be 128 or 256");
+      c->block = int(value);
+      break;
+    case TT_OPT_SEARCH_GRAPH:
+      c->use_graph = value != 0;
+      break;
+    default:
+      return tt_fail(c, TT_ERR_INVALID_ARG, "unknown option %d", option);
+  }
+  tt_ctx_drop_graph(c);
+  return TT_OK;
+}
+
+extern "C" tt_status tt_ctx_get_option(const tt_ctx* c, int32_t option, int64_t* value) {
+  if (!c || !value) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx or value is NULL");
+  switch (option) {
+    case TT_OPT_KERNEL: *value = c->kernel; return TT_OK;
+    case TT_OPT_BLOCK: *value = c->block; return TT_OK;
+    case TT_OPT_SEARCH_GRAPH: *value = c->use_graph ? 1 : 0; return TT_OK;
+  }
+  return tt_fail(nullptr, TT_ERR_INVALID_ARG, "unknown option %d", option);
+}
+
+extern "C" tt_status tt_ctx_autotune(tt_ctx* c, const float* theta, int32_t P, float* S,
+                                     float* times_ms, void* stream) {
+  if (!c) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  if (P < 1) return tt_fail(c, TT_ERR_INVALID_ARG, "P must be >= 1");
+  if (c->n_dom > 0 && (!theta || !S)) return tt_fail(c, TT_ERR_INVALID_ARG, "NULL array");
+  static const int cand[TT_N_TUNE_CANDIDATES][2] = {
+      {TT_KERNEL_PACKED, 256},     {TT_KERNEL_PACKED, 128}, {TT_KERNEL_PERSISTENT, 256},
+      {TT_KERNEL_PERSISTENT, 128}, {TT_KERNEL_SCALAR, 256}, {TT_KERNEL_SCALAR, 128}};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  cudaError_t r = cudaEventCreate(&e0);
+  if (r == cudaSuccess) r = cudaEventCreate(&e1);
+  if (r != cudaSuccess) return tt_cuda_check(c, r, "event create");
+  int best = 0;
+  float best_ms = 0.f;
+  tt_status st = TT_OK;
+  for (int i = 0; i < TT_N_TUNE_CANDIDATES && st == TT_OK; ++i) {
+    tt::EvalArgs a = c->eval_args(theta, P, S);
+    a.kernel = cand[i][0];
+    a.block = cand[i][1];
+    r = tt::launch_semblance(a, s);  // warm-up
+    if (r == cudaSuccess) r = cudaEventRecord(e0, s);
+    for (int k = 0; k < 3 && r == cudaSuccess; ++k) r = tt::launch_semblance(a, s);
+    if (r == cudaSuccess) r = cudaEventRecord(e1, s);
+    if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+    if (r != cudaSuccess) {
+      st = tt_cuda_check(c, r, "autotune");
+      break;
+    }
+    ms /= 3.f;
+    if (times_ms) times_ms[i] = ms;
+    if (i == 0 || ms < best_ms) {
+      best = i;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TT_OK) return st;
+  c->kernel = cand[best][0];
+  c->block = cand[best][1];
+  tt_ctx_drop_graph(c);
+  return TT_OK;
 }
 
 cudaError_t tt_ctx::semblance(const tt::EvalArgs& a, cudaStream_t s, bool grad) {
@@ -207,10 +297,13 @@ void free_ctx(tt_ctx* c) {
   void* ptrs[] = {c->traces, c->mid, c->off, c->stage, c->g_inv_dt, c->ap_ptr, c->ap_tab,
                   c->dom_it0, c->dom_group, c->bounds, c->pop, c->fit, c->trial[0],
                   c->trial[1], c->tfit[0], c->tfit[1], c->snap, c->imports, c->slots,
-                  c->best_idx, c->pol_th, c->pol_g, c->pol_S, c->pol_bth, c->pol_bS, c->d_err};
+                  c->best_idx, c->pol_th, c->pol_g, c->pol_S, c->pol_bth, c->pol_bS, c->d_err,
+                  c->queue, c->out_th, c->out_S};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto e : c->ev) cudaEventDestroy(e);
+  tt_ctx_drop_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 
@@ -432,8 +525,11 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
     TRY(dalloc(&c->slots, nd * 4), "alloc slots");
     TRY(dalloc(&c->best_idx, nd), "alloc best");
   }
+  TRY(dalloc(&c->queue, 1), "alloc queue");
   {
     size_t nd = size_t(c->n_dom), Dz = size_t(D);
+    TRY(dalloc(&c->out_th, nd * Dz), "alloc search output");
+    TRY(dalloc(&c->out_S, nd), "alloc search output");
     TRY(dalloc(&c->pol_th, nd * Dz), "alloc polish");
     TRY(dalloc(&c->pol_g, nd * Dz), "alloc polish");
     TRY(dalloc(&c->pol_S, nd), "alloc polish");

@@ -63,13 +63,11 @@ extern "C" tt_status tt_polish(tt_ctx* c, float* theta, float* S, int32_t steps,
   return polish_impl(c, theta, theta, S, steps, lr, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" tt_status tt_search(tt_ctx* c, float* best_theta, float* best_S, uint64_t* n_evals,
-                               void* stream) {
-  if (!c) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
-  if (!c->has_cfg) return tt_fail(c, TT_ERR_INVALID_ARG, "context was created without a cfg");
-  if (c->n_dom > 0 && (!best_theta || !best_S))
-    return tt_fail(c, TT_ERR_INVALID_ARG, "NULL output array");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+namespace {
+
+// Enqueue the whole search on `s`, writing the result to (best_theta, best_S).
+tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t s,
+                      unsigned long long* n_evals) {
   const tt_de_cfg& cfg = c->cfg;
   const int NP = cfg.np, NG = cfg.ng;
   const bool grid = cfg.exch_every > 0 && c->n_m0 > 0 && c->n_t0 > 0 &&
@@ -144,6 +142,66 @@ extern "C" tt_status tt_search(tt_ctx* c, float* best_theta, float* best_S, uint
     if (st != TT_OK) return st;
     evals += (unsigned long long)c->n_dom * (cfg.polish_steps + 1);
   }
-  if (n_evals) *n_evals = evals;
+  *n_evals = evals;
+  return TT_OK;
+}
+
+}  // namespace
+
+extern "C" tt_status tt_search(tt_ctx* c, float* best_theta, float* best_S, uint64_t* n_evals,
+                               void* stream) {
+  if (!c) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->has_cfg) return tt_fail(c, TT_ERR_INVALID_ARG, "context was created without a cfg");
+  if (c->n_dom > 0 && (!best_theta || !best_S))
+    return tt_fail(c, TT_ERR_INVALID_ARG, "NULL output array");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long evals = 0;
+  if (!c->use_graph || c->profiling || c->n_dom == 0) {
+    tt_status st = search_body(c, best_theta, best_S, s, &evals);
+    if (st == TT_OK && n_evals) *n_evals = evals;
+    return st;
+  }
+  if (!c->graph_exec) {
+    // capture once on a private stream into context-owned outputs; the
+    // counters advanced during capture are moved to the per-replay deltas
+    if (!c->cap_stream) {
+      cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return tt_cuda_check(c, e, "capture stream");
+    }
+    const unsigned long long l0 = c->n_launch, s0 = c->n_sem;
+    const double t0 = c->trace_evals;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return tt_cuda_check(c, e, "begin capture");
+    tt_status st = search_body(c, c->out_th, c->out_S, c->cap_stream, &c->g_evals);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (st == TT_OK && e != cudaSuccess) st = tt_cuda_check(c, e, "end capture");
+    if (st == TT_OK) {
+      e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+      if (e != cudaSuccess) {
+        c->graph_exec = nullptr;
+        st = tt_cuda_check(c, e, "graph instantiate");
+      }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    c->g_launch = c->n_launch - l0;
+    c->g_sem = c->n_sem - s0;
+    c->g_trace_evals = c->trace_evals - t0;
+    c->n_launch = l0;
+    c->n_sem = s0;
+    c->trace_evals = t0;
+    if (st != TT_OK) return st;
+  }
+  cudaError_t e = cudaGraphLaunch(c->graph_exec, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(best_theta, c->out_th, size_t(c->n_dom) * c->D * 4,
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(best_S, c->out_S, size_t(c->n_dom) * 4, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return tt_cuda_check(c, e, "graph launch");
+  c->n_launch += c->g_launch;
+  c->n_sem += c->g_sem;
+  c->trace_evals += c->g_trace_evals;
+  if (n_evals) *n_evals = c->g_evals;
   return TT_OK;
 }

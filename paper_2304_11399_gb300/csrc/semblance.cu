@@ -1,21 +1,36 @@
 // Semblance of a traveltime operator (K1) and its adjoint gradient (K2).
 //
-// Work decomposition: one thread per (domain, individual) pair, pairs laid
-// out domain-major so that a warp covers consecutive individuals of one
-// domain (P >= 32) or several consecutive domains of one group (P < 32).
-// Consecutive domains share a group (same m0, same aperture), so every lane
-// of a warp walks the same aperture entries in the same order: the
-// geometry-table loads are warp-uniform broadcasts and the 2w+2 samples that
-// each lane reads from a trace row sit at nearby addresses for nearby t0 and
-// for a converging population, which the L1 cache turns into reuse.
+// Work decomposition: (domain, individual) pairs are laid out domain-major;
+// a warp owns 64 consecutive pairs, so with NP = 64 it covers one domain,
+// and consecutive warps cover adjacent t0 at the same m0. Consecutive
+// domains share a group (same m0, same aperture), so every lane of a warp
+// walks the same aperture entries in the same order: the geometry-table load
+// is a warp-uniform broadcast and the 2w+2 samples each lane reads from a
+// trace row sit at nearby addresses for nearby t0 and for a converging
+// population, which the L1 cache turns into reuse.
 //
-// Per aperture trace i (Sec. 2, the W_l x T_a inner loop of eq. order):
-//   U = (it0 + (A/dt) dm)^2 + (B/dt^2) dm^2 + (C/dt^2) h^2   (samples^2)
-//   u = min(sqrt(U), ns + w)  -- NaN from U < 0 also maps to ns + w, where
-//                                the whole window reads padding zeros
-//   j = floor(u), f = u - j, a_k = x[j+k] + f (x[j+k+1] - x[j+k])
-//   s_k += a_k, E += a_k^2
-// S = sum_k s_k^2 / (N E) (0 when E = 0).
+// Per aperture trace i (Sec. 2, the W_l x T_a inner loop of eq. order), in
+// sample units (A' = A/dt, B' = B/dt^2, C' = C/dt^2, p0 = it0), the position
+// u = t/dt of the window centre is found, then
+//   j = floor(u), f = u - j, g = 1 - f,
+//   a_k = g x[j+k] + f x[j+k+1],  s_k += a_k,  E += a_k^2
+// and S = sum_k s_k^2 / (N E) (0 when E = 0).
+//
+// Two ways to find u, chosen by the record length at launch:
+//  * direct (records up to 2048 samples, u <= 2048 + w):
+//      q = p0 + A' dm,  U = q^2 + B' dm^2 + C' h^2,  u = sqrt(U)
+//    whose FP32 rounding stays within ~1e-4 samples there;
+//  * moveout (longer records): u = p0 + du with du the root of
+//      du^2 + 2 p0 du - V = 0,  V = x (x + 2 p0) + B' dm^2 + C' h^2,  x = A' dm,
+//    taken as du0 = U r - p0 (r ~ U^-1/2 from the hardware, one rounding)
+//    refined by one Newton step du = du0 - (du0 (du0 + 2 p0) - V) r / 2.
+//    p0 is an exact integer and du is tens of samples for deep events, so
+//    the fraction keeps ~1e-5-sample accuracy where u itself (thousands of
+//    samples) would round at ~1e-4 samples.
+// U < 0 (no real traveltime) gives NaN, which the clamp maps to ns + w: a
+// window of padding zeros. The scalar and the packed code run the same
+// operations; no product is ever rounded and then added (a pattern a compiler
+// may fuse), so they agree bit for bit.
 #include "tt_internal.cuh"
 
 namespace tt {
@@ -24,6 +39,12 @@ namespace {
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
@@ -39,24 +60,27 @@ __device__ __forceinline__ float ld_sample<__nv_bfloat16>(const __nv_bfloat16* p
   return __uint_as_float(unsigned(u) << 16);
 }
 
-// Per-lane prologue shared by K1 and K2.
+// Per-lane constants of one (domain, individual) pair.
 struct Lane {
-  int d, p, e0, e1;
+  int d, e0, e1, p0i;
   float p0, ca, cb, cc, inv_dt;
+  float two_p0, p0sq;  // 2 p0, p0^2 + 1e-30 (the bias keeps U = 0 finite under rsqrt)
+  float lim, neg_p0;   // moveout: du is clamped to [-p0, ns + w - p0]
+  float umax;          // direct: u is clamped to ns + w
 };
 
 template <int OP>
 __device__ __forceinline__ bool lane_setup(const EvalArgs& a, long long q, Lane& L) {
   if (q >= (long long)a.n_dom * a.P) return false;
   L.d = int(q / a.P);
-  L.p = int(q - (long long)L.d * a.P);
-  int g = a.dom_group[L.d];
+  const int g = a.dom_group[L.d];
   L.inv_dt = a.g_inv_dt[g];
   L.e0 = a.ap_ptr[g];
   L.e1 = a.ap_ptr[g + 1];
-  L.p0 = float(a.dom_it0[L.d]);
+  L.p0i = a.dom_it0[L.d];
+  L.p0 = float(L.p0i);
   const float* th = a.theta + q * (OP == TT_OP_CMP ? 1 : 3);
-  float i2 = L.inv_dt * L.inv_dt;
+  const float i2 = L.inv_dt * L.inv_dt;
   if (OP == TT_OP_CMP) {
     L.ca = 0.f;
     L.cb = 0.f;
@@ -66,17 +90,64 @@ __device__ __forceinline__ bool lane_setup(const EvalArgs& a, long long q, Lane&
     L.cb = th[1] * i2;
     L.cc = th[2] * i2;
   }
+  L.two_p0 = 2.f * L.p0;
+  L.p0sq = __fmul_rn(L.p0, L.p0) + 1e-30f;
+  L.lim = a.umax - L.p0;
+  L.neg_p0 = -L.p0;
+  L.umax = a.umax;
   return true;
 }
 
-template <int OP>
-__device__ __forceinline__ float position_sq(const Lane& L, float4 t4, float& qv) {
-  if (OP == TT_OP_CMP) {
-    qv = L.p0;
-    return fmaf(L.cc, t4.z, __fmul_rn(L.p0, L.p0));
+// Position of one pair on one trace. Every operation is rounded once, in the
+// same order as one lane of the packed path, so both give identical bits.
+struct Pos {
+  int j;       // window sample k sits at j - W + k
+  float f, g;  // interpolation weights
+  float u;     // clamped position (samples)
+  float q;     // p0 + A' dm (for the gradient)
+};
+
+template <int OP, bool MOVEOUT>
+__device__ __forceinline__ Pos locate(const Lane& L, float4 t4) {
+  Pos P;
+  if (!MOVEOUT) {
+    float U;
+    if (OP == TT_OP_CMP) {
+      P.q = L.p0;
+      U = fmaf(L.cc, t4.z, __fmul_rn(L.p0, L.p0));
+    } else {
+      P.q = fmaf(L.ca, t4.x, L.p0);
+      U = fmaf(L.cb, t4.y, fmaf(L.cc, t4.z, __fmul_rn(P.q, P.q)));
+    }
+    P.u = fminf(sqrt_approx(U), L.umax);
+    const float fl = truncf(P.u);
+    P.f = __fsub_rn(P.u, fl);
+    P.g = __fsub_rn(1.f, P.f);
+    P.j = int(fl);
+    return P;
   }
-  qv = fmaf(L.ca, t4.x, L.p0);
-  return fmaf(L.cb, t4.y, fmaf(L.cc, t4.z, __fmul_rn(qv, qv)));
+  float V, x;
+  if (OP == TT_OP_CMP) {
+    x = 0.f;
+    V = __fmul_rn(L.cc, t4.z);
+  } else {
+    x = __fmul_rn(L.ca, t4.x);
+    const float w = fmaf(L.cb, t4.y, __fmul_rn(L.cc, t4.z));
+    V = fmaf(x, __fadd_rn(x, L.two_p0), w);
+  }
+  const float U = __fadd_rn(L.p0sq, V);
+  const float r = rsqrt_approx(U);
+  const float du0 = fmaf(U, r, L.neg_p0);
+  const float res = fmaf(du0, __fadd_rn(du0, L.two_p0), __fmul_rn(V, -1.f));
+  float du = fmaf(res, __fmul_rn(r, -0.5f), du0);
+  du = fmaxf(fminf(du, L.lim), L.neg_p0);
+  const float fl = floorf(du);
+  P.f = fmaf(fl, -1.f, du);
+  P.g = fmaf(P.f, -1.f, 1.f);
+  P.j = L.p0i + int(fl);
+  P.u = L.p0 + du;
+  P.q = L.p0 + x;
+  return P;
 }
 
 // Final normalisation S = Q / (N E). FP32-stored traces: E is one FP32
@@ -101,8 +172,17 @@ __device__ __forceinline__ float normalise(float Q, int N, float E, double Ed) {
   return (E > 0.f) ? Q / (float(N) * E) : 0.f;
 }
 
+__device__ __forceinline__ void store_S(const EvalArgs& a, long long q, int d, float S) {
+  if (a.slots) {
+    const int slot = a.slots[q];
+    if (slot >= 0) a.S[(size_t)d * a.np_out + slot] = S;
+  } else {
+    a.S[q] = S;
+  }
+}
+
 // Scalar evaluation of one (domain, individual) pair over its aperture.
-template <int OP, int W, typename T>
+template <int OP, int W, typename T, bool MV>
 __device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
   constexpr int K = 2 * W + 1;
   const T* __restrict__ tr = static_cast<const T*>(a.traces);
@@ -116,19 +196,14 @@ __device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
     float Ec = 0.f;
     for (int e = c0; e < c1; ++e) {
       const float4 t4 = __ldg(a.ap_tab + e);
-      float qv;
-      const float U = position_sq<OP>(L, t4, qv);
-      const float u = fminf(sqrt_approx(U), a.umax);
-      const float fl = truncf(u);
-      const float f = u - fl, g = 1.f - f;
-      const T* x = tr + (__float_as_uint(t4.w) + int(fl) - W);
+      const Pos P = locate<OP, MV>(L, t4);
+      const T* x = tr + (__float_as_uint(t4.w) + P.j - W);
       float xv[K + 1];
 #pragma unroll
       for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        // same operations, in the same order, as one lane of the packed path
-        const float ak = fmaf(f, xv[k + 1], __fmul_rn(g, xv[k]));
+        const float ak = fmaf(P.f, xv[k + 1], __fmul_rn(P.g, xv[k]));
         s[k] = __fadd_rn(s[k], ak);
         Ec = fmaf(ak, ak, Ec);
       }
@@ -138,88 +213,105 @@ __device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
   float Q = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
-  const int N = L.e1 - L.e0;
-  return normalise<T>(Q, N, E, Ed);
+  return normalise<T>(Q, L.e1 - L.e0, E, Ed);
 }
 
-__device__ __forceinline__ void store_S(const EvalArgs& a, long long q, int d, float S) {
-  if (a.slots) {
-    const int slot = a.slots[q];
-    if (slot >= 0) a.S[(size_t)d * a.np_out + slot] = S;
-  } else {
-    a.S[q] = S;
-  }
-}
-
-// K1. Each thread evaluates two (domain, individual) pairs, q and q + 32 of
-// its warp's 64 consecutive pairs. When both lie in one group (the common
-// case: same aperture, possibly different t0) the aperture is walked once
-// and the two windows are processed with packed FP32x2 arithmetic: sample
-// k of the two pairs forms one register pair, so every interpolation,
-// stack and energy update is one f32x2 instruction for both. Otherwise
-// (a group boundary inside the warp, or no second pair) each pair is
-// evaluated on its own.
-template <int OP, int W, typename T>
-__global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
+// One 64-pair unit: each thread evaluates pairs q and q + 32. When both lie
+// in one group (the common case: same aperture, possibly different t0) the
+// aperture is walked once and the two windows are processed with packed
+// FP32x2 arithmetic: sample k of the two pairs forms one register pair, so
+// every interpolation, stack and energy update is one f32x2 instruction for
+// both. Otherwise (a group boundary inside the warp, or no second pair) each
+// pair is evaluated on its own (same operations, same bits).
+template <int OP, int W, typename T, bool MV>
+__device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int lane) {
   constexpr int K = 2 * W + 1;
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const long long q0 = warp * 64 + lane, q1 = q0 + 32;
+  const long long q0 = unit * 64 + lane, q1 = q0 + 32;
   Lane L0, L1;
-  const bool v0 = lane_setup<OP>(a, q0, L0);
-  if (!v0) return;
+  if (!lane_setup<OP>(a, q0, L0)) return;
   const bool v1 = lane_setup<OP>(a, q1, L1);
   if (!v1 || L1.e0 != L0.e0 || L1.e1 != L0.e1 || L1.inv_dt != L0.inv_dt) {
-    store_S(a, q0, L0.d, eval_scalar<OP, W, T>(a, L0));
-    if (v1) store_S(a, q1, L1.d, eval_scalar<OP, W, T>(a, L1));
+    store_S(a, q0, L0.d, eval_scalar<OP, W, T, MV>(a, L0));
+    if (v1) store_S(a, q1, L1.d, eval_scalar<OP, W, T, MV>(a, L1));
     return;
   }
   const T* __restrict__ tr = static_cast<const T*>(a.traces);
   const float2 ca = make_float2(L0.ca, L1.ca), cb = make_float2(L0.cb, L1.cb),
-               cc = make_float2(L0.cc, L1.cc), p0 = make_float2(L0.p0, L1.p0);
-  const float2 p0sq = __fmul2_rn(p0, p0);
+               cc = make_float2(L0.cc, L1.cc), two_p0 = make_float2(L0.two_p0, L1.two_p0),
+               p0sq = make_float2(L0.p0sq, L1.p0sq), neg_p0 = make_float2(L0.neg_p0, L1.neg_p0),
+               p0v = make_float2(L0.p0, L1.p0);
+  const float2 p0p0 = __fmul2_rn(p0v, p0v);
+  const float2 m1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f),
+               mhalf = make_float2(-0.5f, -0.5f);
   float2 s[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) s[k] = make_float2(0.f, 0.f);
   float2 E = make_float2(0.f, 0.f);
   double Ed0 = 0.0, Ed1 = 0.0;  // FP64 chunk sums (BF16 storage only)
   for (int c0 = L0.e0, c1; c0 < L0.e1; c0 = c1) {
-  c1 = (L0.e1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : L0.e1;
-  float2 Ec = make_float2(0.f, 0.f);
-  for (int e = c0; e < c1; ++e) {
-    const float4 t4 = __ldg(a.ap_tab + e);
-    float2 U;
-    if (OP == TT_OP_CMP) {
-      U = __ffma2_rn(cc, make_float2(t4.z, t4.z), p0sq);
+    c1 = (L0.e1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : L0.e1;
+    float2 Ec = make_float2(0.f, 0.f);
+    for (int e = c0; e < c1; ++e) {
+      const float4 t4 = __ldg(a.ap_tab + e);
+      float2 f, g;
+      int j0, j1;
+      if constexpr (!MV) {
+        float2 U;
+        if (OP == TT_OP_CMP) {
+          U = __ffma2_rn(cc, make_float2(t4.z, t4.z), p0p0);
+        } else {
+          const float2 qv = __ffma2_rn(ca, make_float2(t4.x, t4.x), p0v);
+          U = __ffma2_rn(cc, make_float2(t4.z, t4.z), __fmul2_rn(qv, qv));
+          U = __ffma2_rn(cb, make_float2(t4.y, t4.y), U);
+        }
+        const float u0 = fminf(sqrt_approx(U.x), L0.umax), u1 = fminf(sqrt_approx(U.y), L1.umax);
+        const float fl0 = truncf(u0), fl1 = truncf(u1);
+        f = make_float2(__fsub_rn(u0, fl0), __fsub_rn(u1, fl1));
+        g = make_float2(__fsub_rn(1.f, f.x), __fsub_rn(1.f, f.y));
+        j0 = int(fl0);
+        j1 = int(fl1);
+      } else {
+        float2 V;
+        if (OP == TT_OP_CMP) {
+          V = __fmul2_rn(cc, make_float2(t4.z, t4.z));
+        } else {
+          const float2 x = __fmul2_rn(ca, make_float2(t4.x, t4.x));
+          const float2 w = __ffma2_rn(cb, make_float2(t4.y, t4.y),
+                                      __fmul2_rn(cc, make_float2(t4.z, t4.z)));
+          V = __ffma2_rn(x, __fadd2_rn(x, two_p0), w);
+        }
+        const float2 U = __fadd2_rn(p0sq, V);
+        const float2 r = make_float2(rsqrt_approx(U.x), rsqrt_approx(U.y));
+        const float2 du0 = __ffma2_rn(U, r, neg_p0);
+        const float2 res = __ffma2_rn(du0, __fadd2_rn(du0, two_p0), __fmul2_rn(V, m1));
+        float2 du = __ffma2_rn(res, __fmul2_rn(r, mhalf), du0);
+        du.x = fmaxf(fminf(du.x, L0.lim), L0.neg_p0);
+        du.y = fmaxf(fminf(du.y, L1.lim), L1.neg_p0);
+        const float2 fl = make_float2(floorf(du.x), floorf(du.y));
+        f = __ffma2_rn(fl, m1, du);
+        g = __ffma2_rn(f, m1, one);
+        j0 = L0.p0i + int(fl.x);
+        j1 = L1.p0i + int(fl.y);
+      }
+      const unsigned base = __float_as_uint(t4.w) - W;
+      const T* x0 = tr + (base + j0);
+      const T* x1 = tr + (base + j1);
+      float2 xv[K + 1];
+#pragma unroll
+      for (int k = 0; k <= K; ++k) xv[k] = make_float2(ld_sample<T>(x0 + k), ld_sample<T>(x1 + k));
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float2 ak = __ffma2_rn(f, xv[k + 1], __fmul2_rn(g, xv[k]));
+        s[k] = __fadd2_rn(s[k], ak);
+        Ec = __ffma2_rn(ak, ak, Ec);
+      }
+    }
+    if (Chunk<T>::kF64) {
+      Ed0 += double(Ec.x);
+      Ed1 += double(Ec.y);
     } else {
-      const float2 qv = __ffma2_rn(ca, make_float2(t4.x, t4.x), p0);
-      U = __ffma2_rn(cc, make_float2(t4.z, t4.z), __fmul2_rn(qv, qv));
-      U = __ffma2_rn(cb, make_float2(t4.y, t4.y), U);
+      E = Ec;
     }
-    const float u0 = fminf(sqrt_approx(U.x), a.umax);
-    const float u1 = fminf(sqrt_approx(U.y), a.umax);
-    const float fl0 = truncf(u0), fl1 = truncf(u1);
-    const float2 f = make_float2(u0 - fl0, u1 - fl1);
-    const float2 g = make_float2(1.f - f.x, 1.f - f.y);
-    const unsigned base = __float_as_uint(t4.w) - W;
-    const T* x0 = tr + (base + int(fl0));
-    const T* x1 = tr + (base + int(fl1));
-    float2 xv[K + 1];
-#pragma unroll
-    for (int k = 0; k <= K; ++k) xv[k] = make_float2(ld_sample<T>(x0 + k), ld_sample<T>(x1 + k));
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float2 ak = __ffma2_rn(f, xv[k + 1], __fmul2_rn(g, xv[k]));
-      s[k] = __fadd2_rn(s[k], ak);
-      Ec = __ffma2_rn(ak, ak, Ec);
-    }
-  }
-  if (Chunk<T>::kF64) {
-    Ed0 += double(Ec.x);
-    Ed1 += double(Ec.y);
-  } else {
-    E = Ec;
-  }
   }
   float2 Q = make_float2(0.f, 0.f);
 #pragma unroll
@@ -229,17 +321,46 @@ __global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
   store_S(a, q1, L1.d, normalise<T>(Q.y, N, E.y, Ed1));
 }
 
+// K1, grid-mapped (queue == nullptr: one 64-pair unit per warp, the grid
+// covers every unit) or persistent (a grid sized to the GPU; after its first
+// unit a warp takes the next one from an atomic counter, so warps whose
+// apertures are short take more units).
+template <int OP, int W, typename T, bool MV>
+__global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long n_units = ((long long)a.n_dom * a.P + 63) / 64;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  long long unit = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  while (unit < n_units) {
+    eval_unit<OP, W, T, MV>(a, unit, lane);
+    if (!a.queue) break;
+    __syncwarp();
+    unsigned long long next = 0;
+    if (lane == 0) next = atomicAdd(a.queue, 1ull);
+    unit = warps + (long long)__shfl_sync(0xffffffffu, next, 0);
+  }
+}
+
+// K1, one (domain, individual) pair per thread.
+template <int OP, int W, typename T, bool MV>
+__global__ void __launch_bounds__(kBlock) k_semblance_scalar(const EvalArgs a) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  Lane L;
+  if (!lane_setup<OP>(a, q, L)) return;
+  store_S(a, q, L.d, eval_scalar<OP, W, T, MV>(a, L));
+}
+
 // K2: two passes over the aperture. Pass 1 = K1 (s_k, E, S). With
 // alpha = 2/(N E), beta = 2 S / E, dS/da_ik = alpha s_k - beta a_ik, so pass 2
 // forms dS/du_i = sum_k (alpha s_k - beta a_ik)(x[j+k+1] - x[j+k]) and
-// chains it through du/dtheta:
-//   du/dA = (it0 + A dm/dt) dm / (u dt),  du/dB = dm^2 / (2 u dt^2),
-//   du/dC = h^2 / (2 u dt^2).
-template <int OP, int W, typename T>
+// chains it through du/dtheta (u = p0 + du in samples, q = p0 + A' dm):
+//   du/dA = q dm / (u dt),  du/dB = dm^2 / (2 u dt^2),  du/dC = h^2 / (2 u dt^2).
+// Positions clamped to the all-zero window and u = 0 contribute nothing.
+template <int OP, int W, typename T, bool MV>
 __global__ void __launch_bounds__(kBlock) k_semblance_grad(const EvalArgs a) {
   constexpr int K = 2 * W + 1;
   constexpr int D = OP == TT_OP_CMP ? 1 : 3;
-  const long long q = (long long)blockIdx.x * kBlock + threadIdx.x;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   Lane L;
   if (!lane_setup<OP>(a, q, L)) return;
   const T* __restrict__ tr = static_cast<const T*>(a.traces);
@@ -249,17 +370,14 @@ __global__ void __launch_bounds__(kBlock) k_semblance_grad(const EvalArgs a) {
   float E = 0.f;
   for (int e = L.e0; e < L.e1; ++e) {
     const float4 t4 = __ldg(a.ap_tab + e);
-    float qv;
-    const float u = fminf(sqrt_approx(position_sq<OP>(L, t4, qv)), a.umax);
-    const float fl = truncf(u);
-    const float f = u - fl;
-    const T* x = tr + (__float_as_uint(t4.w) + int(fl) - W);
+    const Pos P = locate<OP, MV>(L, t4);
+    const T* x = tr + (__float_as_uint(t4.w) + P.j - W);
     float xv[K + 1];
 #pragma unroll
     for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const float ak = fmaf(f, xv[k + 1] - xv[k], xv[k]);
+      const float ak = fmaf(P.f, xv[k + 1], __fmul_rn(P.g, xv[k]));
       s[k] += ak;
       E = fmaf(ak, ak, E);
     }
@@ -275,11 +393,8 @@ __global__ void __launch_bounds__(kBlock) k_semblance_grad(const EvalArgs a) {
     const float beta = 2.f * S / E;
     for (int e = L.e0; e < L.e1; ++e) {
       const float4 t4 = __ldg(a.ap_tab + e);
-      float qv;
-      const float u = fminf(sqrt_approx(position_sq<OP>(L, t4, qv)), a.umax);
-      const float fl = truncf(u);
-      const float f = u - fl;
-      const T* x = tr + (__float_as_uint(t4.w) + int(fl) - W);
+      const Pos P = locate<OP, MV>(L, t4);
+      const T* x = tr + (__float_as_uint(t4.w) + P.j - W);
       float xv[K + 1];
 #pragma unroll
       for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
@@ -287,15 +402,15 @@ __global__ void __launch_bounds__(kBlock) k_semblance_grad(const EvalArgs a) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float gk = xv[k + 1] - xv[k];
-        const float ak = fmaf(f, gk, xv[k]);
+        const float ak = fmaf(P.f, xv[k + 1], __fmul_rn(P.g, xv[k]));
         sg = fmaf(s[k], gk, sg);
         ag = fmaf(ak, gk, ag);
       }
       const float dSdu = fmaf(alpha, sg, -beta * ag);
-      const float inv_u = (u > 0.f && u < a.umax) ? 1.f / u : 0.f;
+      const float inv_u = (P.u > 0.f && P.u < L.umax) ? 1.f / P.u : 0.f;
       const float c = dSdu * inv_u;
       if (OP == TT_OP_CRS) {
-        G0 = fmaf(c * qv, t4.x, G0);
+        G0 = fmaf(c * P.q, t4.x, G0);
         G1 = fmaf(0.5f * c, t4.y, G1);
       }
       G2 = fmaf(0.5f * c, t4.z, G2);
@@ -315,56 +430,78 @@ __global__ void __launch_bounds__(kBlock) k_semblance_grad(const EvalArgs a) {
 
 using KFn = void (*)(const EvalArgs);
 
-template <int OP, typename T>
-KFn pick_fwd(int W) {
-  switch (W) {
-    case 0: return k_semblance<OP, 0, T>;
-    case 1: return k_semblance<OP, 1, T>;
-    case 2: return k_semblance<OP, 2, T>;
-    case 3: return k_semblance<OP, 3, T>;
-    case 4: return k_semblance<OP, 4, T>;
-    case 5: return k_semblance<OP, 5, T>;
-    case 6: return k_semblance<OP, 6, T>;
-    case 7: return k_semblance<OP, 7, T>;
-    case 8: return k_semblance<OP, 8, T>;
-  }
-  return nullptr;
-}
+constexpr int kDirectMax = 2048;  // direct position up to u = 2048 samples
 
-template <int OP, typename T>
-KFn pick_grad(int W) {
-  switch (W) {
-    case 0: return k_semblance_grad<OP, 0, T>;
-    case 1: return k_semblance_grad<OP, 1, T>;
-    case 2: return k_semblance_grad<OP, 2, T>;
-    case 3: return k_semblance_grad<OP, 3, T>;
-    case 4: return k_semblance_grad<OP, 4, T>;
-    case 5: return k_semblance_grad<OP, 5, T>;
-    case 6: return k_semblance_grad<OP, 6, T>;
-    case 7: return k_semblance_grad<OP, 7, T>;
-    case 8: return k_semblance_grad<OP, 8, T>;
+#define TT_W_TABLE(NAME)                                                                  \
+  template <int OP, typename T, bool MV>                                                  \
+  KFn NAME##_pick(int W) {                                                                \
+    switch (W) {                                                                          \
+      case 0: return NAME<OP, 0, T, MV>;                                                  \
+      case 1: return NAME<OP, 1, T, MV>;                                                  \
+      case 2: return NAME<OP, 2, T, MV>;                                                  \
+      case 3: return NAME<OP, 3, T, MV>;                                                  \
+      case 4: return NAME<OP, 4, T, MV>;                                                  \
+      case 5: return NAME<OP, 5, T, MV>;                                                  \
+      case 6: return NAME<OP, 6, T, MV>;                                                  \
+      case 7: return NAME<OP, 7, T, MV>;                                                  \
+      case 8: return NAME<OP, 8, T, MV>;                                                  \
+    }                                                                                     \
+    return nullptr;                                                                       \
+  }                                                                                       \
+  template <bool MV>                                                                      \
+  KFn NAME##_select2(int op, int storage, int W) {                                        \
+    const bool bf = storage == TT_STORE_BF16;                                             \
+    if (op == TT_OP_CMP)                                                                  \
+      return bf ? NAME##_pick<TT_OP_CMP, __nv_bfloat16, MV>(W)                            \
+                : NAME##_pick<TT_OP_CMP, float, MV>(W);                                   \
+    return bf ? NAME##_pick<TT_OP_CRS, __nv_bfloat16, MV>(W)                              \
+              : NAME##_pick<TT_OP_CRS, float, MV>(W);                                     \
+  }                                                                                       \
+  KFn NAME##_select(int op, int storage, int W, bool mv) {                                \
+    return mv ? NAME##_select2<true>(op, storage, W) : NAME##_select2<false>(op, storage, W); \
   }
-  return nullptr;
-}
 
-KFn select_kernel(const EvalArgs& a, bool grad) {
-  const bool bf = a.storage == TT_STORE_BF16;
-  if (a.op == TT_OP_CMP)
-    return grad ? (bf ? pick_grad<TT_OP_CMP, __nv_bfloat16>(a.W) : pick_grad<TT_OP_CMP, float>(a.W))
-                : (bf ? pick_fwd<TT_OP_CMP, __nv_bfloat16>(a.W) : pick_fwd<TT_OP_CMP, float>(a.W));
-  return grad ? (bf ? pick_grad<TT_OP_CRS, __nv_bfloat16>(a.W) : pick_grad<TT_OP_CRS, float>(a.W))
-              : (bf ? pick_fwd<TT_OP_CRS, __nv_bfloat16>(a.W) : pick_fwd<TT_OP_CRS, float>(a.W));
-}
+TT_W_TABLE(k_semblance)
+TT_W_TABLE(k_semblance_scalar)
+TT_W_TABLE(k_semblance_grad)
+#undef TT_W_TABLE
 
 cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
   const long long n = (long long)a.n_dom * a.P;
   if (n == 0) return cudaSuccess;
-  KFn fn = select_kernel(a, grad);
+  const int block = (a.block == 128) ? 128 : 256;
+  // records longer than kDirectMax samples use the moveout form of the position
+  const bool mv = a.umax > float(kDirectMax);
+  KFn fn;
+  long long blocks;
+  EvalArgs b = a;
+  if (grad) {
+    fn = k_semblance_grad_select(a.op, a.storage, a.W, mv);
+    blocks = (n + block - 1) / block;
+  } else if (a.kernel == TT_KERNEL_SCALAR) {
+    fn = k_semblance_scalar_select(a.op, a.storage, a.W, mv);
+    blocks = (n + block - 1) / block;
+  } else {
+    fn = k_semblance_select(a.op, a.storage, a.W, mv);
+    const long long units = (n + 63) / 64;
+    blocks = (units + block / 32 - 1) / (block / 32);
+    if (a.kernel == TT_KERNEL_PERSISTENT && a.queue) {
+      int dev = 0, sms = 0, per_sm = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0);
+      if (e != cudaSuccess) return e;
+      const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
+      if (resident < blocks) blocks = resident;
+      e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
+      if (e != cudaSuccess) return e;
+    } else {
+      b.queue = nullptr;
+    }
+  }
   if (!fn) return cudaErrorInvalidValue;
-  const long long per_block = grad ? kBlock : 2ll * kBlock;  // K1: two pairs per thread
-  const long long blocks = (n + per_block - 1) / per_block;
   if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-  fn<<<unsigned(blocks), kBlock, 0, s>>>(a);
+  fn<<<unsigned(blocks), block, 0, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,9 @@ struct EvalArgs {
   float* dS;                // [n_dom][P][D] (gradient launches)
   const int* slots;         // scatter mode: result (d, p) -> S[d*np_out + slots[d*P+p]]
   int np_out;
+  int kernel;               // TT_KERNEL_PACKED / _PERSISTENT / _SCALAR (forward launches)
+  int block;                // threads per block: 128 or 256
+  unsigned long long* queue;  // persistent mode: work-unit counter, zero at launch
 };
 
 cudaError_t launch_semblance(const EvalArgs& a, cudaStream_t s);
@@ -94,6 +97,16 @@ struct tt_ctx {
   float *pol_th = nullptr, *pol_g = nullptr, *pol_S = nullptr, *pol_bth = nullptr,
         *pol_bS = nullptr;
   int* d_err = nullptr;     // device-side validation flag
+  unsigned long long* queue = nullptr;  // persistent-kernel work counter
+  // launch configuration (tt_ctx_set_option / tt_ctx_autotune)
+  int kernel = TT_KERNEL_PACKED, block = 256;
+  bool use_graph = true;
+  // CUDA graph of the whole search, captured on first use
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  float *out_th = nullptr, *out_S = nullptr;
+  unsigned long long g_evals = 0, g_launch = 0, g_sem = 0;
+  double g_trace_evals = 0;
   std::string err;
   // counters and optional event timing of semblance launches
   double sum_N = 0;         // sum over domains of the aperture size
@@ -113,4 +126,5 @@ struct tt_ctx {
 };
 
 tt_status tt_fail(tt_ctx* ctx, tt_status code, const char* fmt, ...);
+void tt_ctx_drop_graph(tt_ctx* ctx);
 tt_status tt_cuda_check(tt_ctx* ctx, cudaError_t e, const char* what);

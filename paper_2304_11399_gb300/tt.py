@@ -227,6 +227,46 @@ def tt_search(ctx: Context, best_theta=None, best_S=None, stream=None):
     return best_theta, best_S, int(n.value)
 
 
+_KERNELS = {"packed": L.TT_KERNEL_PACKED, "persistent": L.TT_KERNEL_PERSISTENT,
+            "scalar": L.TT_KERNEL_SCALAR}
+
+
+def tt_ctx_set_option(ctx: Context, option: str, value):
+    """option: "kernel" ("packed" | "persistent" | "scalar"), "block" (128 | 256)
+    or "search_graph" (bool)."""
+    if option == "kernel":
+        code, v = L.TT_OPT_KERNEL, _KERNELS[value]
+    elif option == "block":
+        code, v = L.TT_OPT_BLOCK, int(value)
+    elif option == "search_graph":
+        code, v = L.TT_OPT_SEARCH_GRAPH, 1 if value else 0
+    else:
+        raise ValueError(f"unknown option {option}")
+    _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_set_option(ctx.handle, code, v))
+
+
+def tt_ctx_get_option(ctx: Context, option: str):
+    code = {"kernel": L.TT_OPT_KERNEL, "block": L.TT_OPT_BLOCK,
+            "search_graph": L.TT_OPT_SEARCH_GRAPH}[option]
+    v = C.c_int64()
+    _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_get_option(ctx.handle, code, C.byref(v)))
+    if option == "kernel":
+        return {b: a for a, b in _KERNELS.items()}[v.value]
+    return bool(v.value) if option == "search_graph" else int(v.value)
+
+
+def tt_ctx_autotune(ctx: Context, theta: torch.Tensor, stream=None):
+    """Time every kernel variant on theta [n_dom, P, D]; keep the fastest.
+    Returns {(variant, block): ms}."""
+    P = int(theta.shape[1])
+    tp = _ptr(theta, "theta", shape=(ctx.n_dom, P, ctx.D))
+    S = torch.empty((ctx.n_dom, P), dtype=torch.float32, device=theta.device)
+    times = (C.c_float * L.TT_N_TUNE_CANDIDATES)()
+    _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_autotune(ctx.handle, tp, P, C.c_void_p(S.data_ptr()),
+                                                        times, _stream(stream)))
+    return {cand: float(times[i]) for i, cand in enumerate(L.TUNE_CANDIDATES)}
+
+
 def tt_ctx_profile(ctx: Context, enable: bool = True):
     """Enable or disable event timing of the context's semblance launches."""
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_profile(ctx.handle, 1 if enable else 0))

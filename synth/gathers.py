@@ -199,7 +199,7 @@ def batched_problems(*, n_prob: int, ntr_range, ns_range, dts, seed: int,
     it0s, groups = [], []
     for p in range(n_prob):
         lo, hi = int(ptr[p]), int(ptr[p + 1])
-        m0[p] = 10_000.0 * p
+        m0[p] = 0.0  # problems are independent; a common origin keeps FP32 coordinates exact
         mid[lo:hi] = m0[p] + dcmp * rng.integers(-ap_cmp, ap_cmp + 1, hi - lo)
         off[lo:hi] = doff * rng.integers(0, int(max_off // doff) + 1, hi - lo)
         ns_p, dt_p = int(nsp[p]), float(dtp[p])
