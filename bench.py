@@ -40,13 +40,74 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 def workload_config(wl, n_gpus):
     p = wl.problem
-    sub = "" if p.n_m0 in (0, 200) else f" (first {p.n_m0} CMPs solved)"
-    return {"workload": "CRS line 200 CMP x 48 offsets x 1500 samples (dt 4 ms), "
-                        "aperture +-10 CMP, window 11" + sub,
+    if wl.info is not None:
+        name = (f"{p.n_groups} uneven CRS problems, 16-240 traces and 750-3000 samples "
+                f"(dt 2/4 ms) each, every sample a domain, window 11")
+    else:
+        sub = "" if p.n_m0 in (0, 200) else f" (first {p.n_m0} CMPs solved)"
+        name = ("CRS line 200 CMP x 48 offsets x 1500 samples (dt 4 ms), aperture +-10 CMP, "
+                "window 11" + sub)
+    return {"workload": name,
             "n_dom": p.n_dom, "np": wl.de.np, "ng": wl.de.ng, "exch_every": wl.de.exch_every,
             "polish_steps": wl.de.polish_steps, "storage": wl.storage,
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "1 GPU"}
+
+
+# ------------------------------------------------------------------ ranks
+
+def rank_env():
+    """(world, rank, local_rank) from the torchrun environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest value any rank holds (the job finishes with its slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_dom_per_rank: int, world: int, seconds_per_step: float) -> float:
+    """Whole-job ZO samples/s: every rank solves its own line of n_dom samples."""
+    return world * n_dom_per_rank / seconds_per_step
+
+
+# ------------------------------------------------------------------ accuracy
+
+def recovery(wl, best_theta, tol=0.01):
+    """Fraction of event-centred domains (isolated strong events, truth in
+    bounds) whose recovered A (as a fraction of its range) and C (relative)
+    are within ``tol`` of the exact recentred parameters, and their count."""
+    import synth
+    prob, line = wl.problem, wl.line
+    if line is None or prob.n_m0 * prob.n_t0 != prob.n_dom:
+        return None
+    lo, hi = np.array(wl.de.lo), np.array(wl.de.hi)
+    ev = line.events
+    hits = tried = 0
+    for e in range(len(ev)):
+        c = int(np.argmin(np.abs(line.cmp_x - ev[e, 0])))
+        if c < 15 or c > line.n_cmp - 16 or c >= prob.n_m0 or abs(ev[e, 5]) < 0.7:
+            continue
+        truth = synth.crs_recentre(ev[e], line.cmp_x[c])
+        if truth is None or not (lo[0] < truth[1] < hi[0] and lo[2] < truth[3] < hi[2]):
+            continue
+        it = int(round(truth[0] / wl.dt))
+        others = [synth.crs_recentre(ev[k], line.cmp_x[c]) for k in range(len(ev)) if k != e]
+        if it < 20 or it > prob.n_t0 - 20 or any(o is not None and abs(o[0] - truth[0]) < 0.1
+                                                 for o in others):
+            continue
+        d = c * prob.n_t0 + it
+        tried += 1
+        hits += int(abs(best_theta[d, 0] - truth[1]) <= tol * (hi[0] - lo[0])
+                    and abs(best_theta[d, 2] - truth[3]) <= tol * truth[3])
+    return {"within_1pct": hits, "of": tried}
 
 
 # ------------------------------------------------------------------ clocks
@@ -115,7 +176,7 @@ def time_oracle(wl, prob):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return 0
     from synth import configs
@@ -150,9 +211,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain-FP32 and BF16-stored comparison searches")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--cmps", type=int, default=0,
                     help="solve only the first CMPS midpoints of the line (profiling case)")
+    ap.add_argument("--workload", default="line", choices=["line", "batched"],
+                    help="line: the 200-CMP CRS line (default); batched: 4096 uneven CRS "
+                         "problems (every sample a domain, DE 64 x 80, autotuned kernel)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -160,9 +226,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device(f"cuda:{local}")
@@ -173,16 +237,16 @@ def main():
     import paper_2304_11399_gb300 as tt
     from synth import configs
 
-    wl = configs.crs_line(rank)
+    wl = configs.crs_line(rank) if args.workload == "line" else configs.batched(rank)
     wl.storage = args.storage
-    if args.cmps:
+    if args.cmps and args.workload == "line":
         import synth
         wl.problem = synth.line_problem(wl.line, half_window=5, ap_half=10,
                                         cmps=list(range(args.cmps)))
     prob = wl.problem
     # CPU baseline first (rank 0, N = 1): the oracle as it stands on a sample
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "line":
         sp = oracle_sample(wl)
         secs = time_oracle(wl, sp)
         cpu = {"value": sp.n_dom / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -192,6 +256,12 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, storage=args.storage,
                            device=dev)
+    tuned = None
+    if args.workload == "batched":
+        th = torch.empty((prob.n_dom, wl.de.np, 3), dtype=torch.float32, device=dev)
+        tt.tt_de_step(ctx, 0, th)
+        tuned = {f"{k}/{b}": round(v, 3) for (k, b), v in tt.tt_ctx_autotune(ctx, th).items()}
+        del th
     best_t = torch.empty((prob.n_dom, 3), dtype=torch.float32, device=dev)
     best_s = torch.empty((prob.n_dom,), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 18, dtype=torch.float32, device=dev)  # 256 MiB
@@ -222,12 +292,9 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in ev)
     stats = tt.tt_ctx_stats(ctx, reset=True)
     tt.tt_ctx_profile(ctx, False)
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
+    ms_max = max_over_ranks(ms, world, dev)
     per_step_s = ms_max / 1e3 / args.steps
-    value = world * prob.n_dom / per_step_s
+    value = job_value(prob.n_dom, world, per_step_s)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -244,10 +311,8 @@ def main():
             host_bs.copy_(best_s, non_blocking=True)
             torch.cuda.synchronize()
         barrier()
-        e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(e_s, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * prob.n_dom * args.steps / float(e_s.item()), "unit": UNIT,
+        e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_value(prob.n_dom, world, e_s / args.steps), "unit": UNIT,
                "h2d_bytes_per_step": int(wl.traces.nbytes),
                "d2h_bytes_per_step": int(host_bt.numel() * 4 + host_bs.numel() * 4)}
 
@@ -264,6 +329,39 @@ def main():
                 "per_launch_ms": stats["semblance_ms"] / stats["timed_launches"],
                 "trace_evals_per_s": stats["trace_evals"] / (stats["semblance_ms"] / 1e3),
                 "semblance_share_of_step": stats["semblance_ms"] / ms}
+    # the same search in other forms on the same GPU (rank 0, line workload)
+    comparison = None
+    if rank == 0 and args.workload == "line" and not args.no_compare:
+        import copy
+        torch.cuda.synchronize()
+        comparison = {"optimised_fp32": {"value": value,
+                                         "recovery": recovery(wl, best_t.cpu().numpy())}}
+
+        def one_form(label, storage, kernel, polish, note):
+            w2 = copy.copy(wl)
+            w2.de = copy.copy(wl.de)
+            w2.de.polish_steps = polish
+            c2 = tt.tt_ctx_create(w2.traces, w2.mid, w2.off, prob, w2.de, storage=storage,
+                                  device=dev)
+            tt.tt_ctx_set_option(c2, "kernel", kernel)
+            tt.tt_ctx_set_option(c2, "search_graph", False)
+            tt.tt_search(c2, best_t, best_s)
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tt.tt_search(c2, best_t, best_s)
+            b.record(stream)
+            barrier()
+            secs = a.elapsed_time(b) / 1e3
+            comparison[label] = {"value": prob.n_dom / secs, "note": note,
+                                 "recovery": recovery(w2, best_t.cpu().numpy())}
+            c2.close()
+
+        one_form("plain_fp32", "f32", "scalar", 0,
+                 "one (domain, individual) pair per thread, scalar FP32, no polish, eager")
+        one_form("bf16_stored", "bf16", "packed", wl.de.polish_steps,
+                 "BF16 trace copy, FP32 arithmetic, FP64 chunked energy, polish")
+        comparison["speedup_vs_plain_fp32"] = value / comparison["plain_fp32"]["value"]
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
@@ -272,7 +370,9 @@ def main():
                 "data": "synthetic (seeded Ricker events + Gaussian noise, SNR 3)",
                 "config": workload_config(wl, world), "clocks": clk, "e2e": e2e,
                 "gpu_launches": int(stats["launches"]), "semblance_calls_per_step": n_evals,
-                "roofline": roof, "cpu_baseline": cpu}
+                "roofline": roof, "cpu_baseline": cpu, "comparison": comparison}
+        if tuned:
+            line["config"]["autotune_ms"] = tuned
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -1,0 +1,87 @@
+"""The benchmark's multi-rank logic on CPU: two gloo ranks (world size 2)
+reduce their step times to the maximum, compute the whole-job value, and only
+rank 0 of the reference arm prints."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w, r, lr = bench.rank_env()
+    t = bench.max_over_ranks(1.5 + rank, w)
+    out[rank] = (w, r, lr, t, bench.job_value(300, w, t))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_to_the_slowest():
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    for rank in range(world):
+        w, r, lr, t, v = out[rank]
+        assert (w, r, lr) == (2, rank, rank)
+        assert t == 2.5                      # max over ranks
+        assert v == pytest.approx(2 * 300 / 2.5)
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0", "--gpus", "2"],
+                       capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_single_rank_helpers():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.0, 1) == 3.0
+    assert bench.job_value(300000, 1, 4.0) == 75000.0
+    line = bench.workload_config(__import__("synth").configs.crs_line(0, n_cmp=3, ns=120, tau_max=0.4), 2)
+    assert "replicas x2" in json.dumps(line)
+
+
+def test_recovery_metric_counts_exact_truth():
+    """bench.recovery: the exact recentred parameters at every domain count
+    as recovered; a 2% error in C does not."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import synth
+    from synth import configs
+    wl = configs.crs_line(2, n_cmp=100, ns=400, n_events=10, tau_max=1.4)
+    p = wl.problem
+    th = np.zeros((p.n_dom, 3))
+    for ev in wl.line.events:
+        for c in range(wl.line.n_cmp):
+            tr = synth.crs_recentre(ev, wl.line.cmp_x[c])
+            if tr is None:
+                continue
+            it = int(round(tr[0] / wl.dt))
+            if 0 <= it < p.n_t0:
+                th[c * p.n_t0 + it] = (tr[1], tr[2], tr[3])
+    r = bench.recovery(wl, th)
+    assert r is not None and r["of"] >= 1 and r["within_1pct"] == r["of"]
+    th[:, 2] *= 1.02
+    assert bench.recovery(wl, th)["within_1pct"] == 0
