@@ -67,10 +67,11 @@ def best_index(fit) -> int:
     return best
 
 
-def init_individual(seed, d, i, lo, hi):
-    """Generation-0 individual i of domain d: lo + u (hi - lo) in float32."""
+def init_individual(seed, d, i, lo, hi, gen=0):
+    """Initial individual i of domain d: lo + u (hi - lo) in float32, from the
+    words of counter generation ``gen`` (0 for the search's generation 0)."""
     D = len(lo)
-    w = words(seed, d, 0, i, D)
+    w = words(seed, d, gen, i, D)
     out = np.empty(D, f32)
     for k in range(D):
         out[k] = f32(lo[k]) + unit_float(w[k]) * (f32(hi[k]) - f32(lo[k]))
