@@ -193,6 +193,33 @@ tt_status tt_neighbor_exchange(tt_ctx* ctx, int32_t n_m0, int32_t n_t0, const fl
  * S [n_dom] receives its semblance. Uses the context's scratch. */
 tt_status tt_polish(tt_ctx* ctx, float* theta, float* S, int32_t steps, float lr, void* stream);
 
+/* Evolution by neighborhood similarity in sweep mode (Sec. 3.4-3.6): the
+ * grid's traces (m0) are cut into buckets of n_bucket consecutive traces;
+ * every bucket runs a forward exploration (NP_f x NG_f, seeded with the best
+ * of the same sample on the previous trace) and n_cycle backward-and-forward
+ * cycles (NP_bf x NG_bf, seeded with the bests of samples t-1, t+1, of
+ * sample t on the previous trace of the sweep, and the own best); each stage
+ * estimates every (n_skip+1)-th sample and interpolates the others linearly
+ * in t, keeping the higher semblance (Sec. 3.5). */
+typedef struct tt_ens_cfg {
+  int32_t np_f, ng_f;    /* forward exploration: population, generations      */
+  int32_t np_bf, ng_bf;  /* backward-and-forward stages                       */
+  int32_t n_skip;        /* samples interpolated between estimated ones       */
+  int32_t n_cycle;       /* backward-and-forward cycles (<= 64)               */
+  int32_t n_bucket;      /* traces per bucket (interactive domain), >= 1      */
+  int32_t reserved;
+} tt_ens_cfg;
+
+/* Run the ENS sweep over the context's (m0, t0) grid (n_m0 * n_t0 == n_dom)
+ * with F, CR, seed and bounds from the context's tt_de_cfg, whose np must be
+ * at least np_f and np_bf (both >= 4). Writes best_theta [n_dom][D] and
+ * best_S [n_dom]; *n_evals (host, may be NULL) receives the semblance-call
+ * count of eq. ens_semblance for the estimated and interpolated samples
+ * actually visited. Uses the context's search scratch (not concurrently with
+ * tt_search). Captured into a CUDA graph on first use like tt_search. */
+tt_status tt_ens_search(tt_ctx* ctx, const tt_ens_cfg* cfg, float* best_theta, float* best_S,
+                        uint64_t* n_evals, void* stream);
+
 /* Counters of a context, accumulated on the host since the last reset:
  * `launches` = kernels this context enqueued; `semblance_launches` and
  * `trace_evals` = semblance/gradient launches and the (aperture trace x

@@ -46,6 +46,11 @@ class DECfg(C.Structure):
                 ("polish_lr", C.c_float), ("reserved", I32)]
 
 
+class EnsCfg(C.Structure):
+    _fields_ = [("np_f", I32), ("ng_f", I32), ("np_bf", I32), ("ng_bf", I32), ("n_skip", I32),
+                ("n_cycle", I32), ("n_bucket", I32), ("reserved", I32)]
+
+
 class Stats(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("semblance_launches", C.c_uint64),
                 ("trace_evals", C.c_double), ("semblance_ms", C.c_double),
@@ -72,6 +77,7 @@ SIGNATURES = {
     "tt_ctx_set_option": (I32, [P, I32, C.c_int64]),
     "tt_ctx_get_option": (I32, [P, I32, C.POINTER(C.c_int64)]),
     "tt_ctx_autotune": (I32, [P, P, I32, P, C.POINTER(C.c_float), P]),
+    "tt_ens_search": (I32, [P, C.POINTER(EnsCfg), P, P, C.POINTER(C.c_uint64), P]),
 }
 
 _lib = None

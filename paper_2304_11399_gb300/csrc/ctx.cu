@@ -56,6 +56,7 @@ tt::EvalArgs tt_ctx::eval_args(const float* theta, int P, float* S) const {
   a.dS = nullptr;
   a.slots = nullptr;
   a.np_out = 0;
+  a.dom_map = nullptr;
   a.kernel = kernel;
   a.block = block;
   a.queue = queue;
@@ -66,6 +67,10 @@ void tt_ctx_drop_graph(tt_ctx* c) {
   if (c->graph_exec) {
     cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
+  }
+  if (c->ens_exec) {
+    cudaGraphExecDestroy(c->ens_exec);
+    c->ens_exec = nullptr;
   }
 }
 
@@ -159,7 +164,9 @@ cudaError_t tt_ctx::semblance(const tt::EvalArgs& a, cudaStream_t s, bool grad) 
   }
   ++n_launch;
   ++n_sem;
-  trace_evals += double(a.P) * sum_N;
+  // a mapped (subset) launch is counted at the mean aperture size
+  trace_evals += double(a.P) * (a.dom_map ? sum_N / double(n_dom > 0 ? n_dom : 1) * a.n_dom
+                                          : sum_N);
   return e;
 }
 

@@ -13,74 +13,21 @@ namespace {
 
 constexpr int kWarps = 4;  // domains per block
 
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
-// (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
-// lo(M0 c0)), key bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-  }
-  return c;
-}
-
-// Word n of the stream of (domain d, generation g, individual i).
-struct Words {
-  uint32_t w[8];
-  __device__ Words(uint32_t k0, uint32_t k1, uint32_t d, uint32_t g, uint32_t i, int n) {
-    const uint4 a = philox4x32_10(make_uint4(i, g, d, 0u), k0, k1);
-    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-    if (n > 4) {
-      const uint4 b = philox4x32_10(make_uint4(i, g, d, 1u), k0, k1);
-      w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-    }
-  }
-};
-
-__device__ __forceinline__ float rank_key(float v) { return isnan(v) ? -INFINITY : v; }
-
-// Warp argmax of fit[0..NP) with the lowest index on ties (NaN lowest).
-__device__ int warp_argmax(const float* fit, int NP, int lane) {
-  float bk = -INFINITY;
-  int bi = 0x7fffffff;
-  for (int i = lane; i < NP; i += 32) {
-    const float k = rank_key(fit[i]);
-    if (bi == 0x7fffffff || k > bk) {
-      bk = k;
-      bi = i;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const float ok = __shfl_xor_sync(0xffffffffu, bk, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ok > bk || (ok == bk && oi < bi)) {
-      bk = ok;
-      bi = oi;
-    }
-  }
-  return bi;
-}
-
 __global__ void __launch_bounds__(kWarps * 32) k_de_step(const DeArgs a) {
   extern __shared__ float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d = blockIdx.x * kWarps + warp;
   if (d >= a.n_dom) return;  // uniform per warp
+  const int gd = a.dom_map ? a.dom_map[d] : d;  // global id: the Philox key's domain
+  if (gd < 0) return;
   const int NP = a.NP, D = a.D;
   float* gpop = a.pop + (size_t)d * NP * D;
   float* gfit = a.fit + (size_t)d * NP;
   if (a.gen == 0) {
     for (int i = lane; i < NP; i += 32) {
-      Words w(a.key0, a.key1, uint32_t(d), 0u, uint32_t(i), D);
+      Words w(a.key0, a.key1, uint32_t(gd), 0u, uint32_t(i), D);
       for (int k = 0; k < D; ++k) {
-        const float u = __uint2float_rn(w.w[k] >> 8) * 5.9604644775390625e-8f;  // 2^-24
+        const float u = unit_float(w.w[k]);
         gpop[i * D + k] = __fadd_rn(a.lo[k], __fmul_rn(u, __fsub_rn(a.hi[k], a.lo[k])));
       }
     }
@@ -120,7 +67,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_de_step(const DeArgs a) {
   // (iii) DE/current-to-best/1/bin + JADE bound repair, one rounding per op
   float* gnext = a.next + (size_t)d * NP * D;
   for (int i = lane; i < NP; i += 32) {
-    Words w(a.key0, a.key1, uint32_t(d), uint32_t(a.gen), uint32_t(i), 3 + D);
+    Words w(a.key0, a.key1, uint32_t(gd), uint32_t(a.gen), uint32_t(i), 3 + D);
     int r1 = int(__umulhi(w.w[0], uint32_t(NP - 1)));
     if (r1 >= i) ++r1;
     int r2 = int(__umulhi(w.w[1], uint32_t(NP - 2)));

@@ -69,15 +69,19 @@ struct Lane {
   float umax;          // direct: u is clamped to ns + w
 };
 
+// L.d is the local domain (indexing theta and S); its geometry comes from the
+// global domain dom_map[L.d] when a map is given (a subset evaluation).
 template <int OP>
 __device__ __forceinline__ bool lane_setup(const EvalArgs& a, long long q, Lane& L) {
   if (q >= (long long)a.n_dom * a.P) return false;
   L.d = int(q / a.P);
-  const int g = a.dom_group[L.d];
+  const int gd = a.dom_map ? a.dom_map[L.d] : L.d;
+  if (gd < 0) return false;
+  const int g = a.dom_group[gd];
   L.inv_dt = a.g_inv_dt[g];
   L.e0 = a.ap_ptr[g];
   L.e1 = a.ap_ptr[g + 1];
-  L.p0i = a.dom_it0[L.d];
+  L.p0i = a.dom_it0[gd];
   L.p0 = float(L.p0i);
   const float* th = a.theta + q * (OP == TT_OP_CMP ? 1 : 3);
   const float i2 = L.inv_dt * L.inv_dt;
@@ -216,8 +220,9 @@ __device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
   return normalise<T>(Q, L.e1 - L.e0, E, Ed);
 }
 
-// One 64-pair unit: each thread evaluates pairs q and q + 32. When both lie
-// in one group (the common case: same aperture, possibly different t0) the
+// One 64-pair unit: each thread evaluates pairs q and q + 32 (either may be
+// absent: past the end, or a domain the map skips). When both lie in one
+// group (the common case: same aperture, possibly different t0) the
 // aperture is walked once and the two windows are processed with packed
 // FP32x2 arithmetic: sample k of the two pairs forms one register pair, so
 // every interpolation, stack and energy update is one f32x2 instruction for
@@ -228,10 +233,10 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
   constexpr int K = 2 * W + 1;
   const long long q0 = unit * 64 + lane, q1 = q0 + 32;
   Lane L0, L1;
-  if (!lane_setup<OP>(a, q0, L0)) return;
+  const bool v0 = lane_setup<OP>(a, q0, L0);
   const bool v1 = lane_setup<OP>(a, q1, L1);
-  if (!v1 || L1.e0 != L0.e0 || L1.e1 != L0.e1 || L1.inv_dt != L0.inv_dt) {
-    store_S(a, q0, L0.d, eval_scalar<OP, W, T, MV>(a, L0));
+  if (!v0 || !v1 || L1.e0 != L0.e0 || L1.e1 != L0.e1 || L1.inv_dt != L0.inv_dt) {
+    if (v0) store_S(a, q0, L0.d, eval_scalar<OP, W, T, MV>(a, L0));
     if (v1) store_S(a, q1, L1.d, eval_scalar<OP, W, T, MV>(a, L1));
     return;
   }

@@ -36,6 +36,7 @@ struct EvalArgs {
   float* dS;                // [n_dom][P][D] (gradient launches)
   const int* slots;         // scatter mode: result (d, p) -> S[d*np_out + slots[d*P+p]]
   int np_out;
+  const int* dom_map;       // optional: local domain r -> global domain (-1: skip r)
   int kernel;               // TT_KERNEL_PACKED / _PERSISTENT / _SCALAR (forward launches)
   int block;                // threads per block: 128 or 256
   unsigned long long* queue;  // persistent mode: work-unit counter, zero at launch
@@ -46,6 +47,7 @@ cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s);
 
 struct DeArgs {
   int n_dom, NP, D, gen;
+  const int* dom_map;       // optional: local domain -> global id keying Philox (-1: skip)
   float* pop;
   float* fit;
   const float* trial;
@@ -59,6 +61,66 @@ struct DeArgs {
 };
 
 cudaError_t launch_de_step(const DeArgs& a, cudaStream_t s);
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
+// (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
+// lo(M0 c0)), key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Word n of the stream of (domain d, generation g, individual i).
+struct Words {
+  uint32_t w[8];
+  __device__ Words(uint32_t k0, uint32_t k1, uint32_t d, uint32_t g, uint32_t i, int n) {
+    const uint4 a = philox4x32_10(make_uint4(i, g, d, 0u), k0, k1);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    if (n > 4) {
+      const uint4 b = philox4x32_10(make_uint4(i, g, d, 1u), k0, k1);
+      w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    }
+  }
+};
+
+// Uniform in [0, 1) from a 32-bit word, exact in FP32: (w >> 8) 2^-24.
+__device__ __forceinline__ float unit_float(uint32_t w) {
+  return __uint2float_rn(w >> 8) * 5.9604644775390625e-8f;
+}
+
+__device__ __forceinline__ float rank_key(float v) { return isnan(v) ? -INFINITY : v; }
+
+// Warp argmax of fit[0..NP) with the lowest index on ties (NaN lowest).
+__device__ inline int warp_argmax(const float* fit, int NP, int lane) {
+  float bk = -INFINITY;
+  int bi = 0x7fffffff;
+  for (int i = lane; i < NP; i += 32) {
+    const float k = rank_key(fit[i]);
+    if (bi == 0x7fffffff || k > bk) {
+      bk = k;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float ok = __shfl_xor_sync(0xffffffffu, bk, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ok > bk || (ok == bk && oi < bi)) {
+      bk = ok;
+      bi = oi;
+    }
+  }
+  return bi;
+}
 cudaError_t launch_best_snapshot(int n_dom, int NP, int D, const float* pop, const float* fit,
                                  float* best_theta, float* best_S, cudaStream_t s);
 cudaError_t launch_exchange_plan(int n_m0, int n_t0, int NP, int D, const float* best_theta,
@@ -107,6 +169,11 @@ struct tt_ctx {
   float *out_th = nullptr, *out_S = nullptr;
   unsigned long long g_evals = 0, g_launch = 0, g_sem = 0;
   double g_trace_evals = 0;
+  // CUDA graph of the ENS sweep (tt_ens_search), for the settings in ens_cfg
+  cudaGraphExec_t ens_exec = nullptr;
+  tt_ens_cfg ens_cfg{};
+  unsigned long long ens_calls = 0, ens_launch = 0, ens_sem = 0;
+  double ens_trace_evals = 0;
   std::string err;
   // counters and optional event timing of semblance launches
   double sum_N = 0;         // sum over domains of the aperture size

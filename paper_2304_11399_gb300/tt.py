@@ -227,6 +227,23 @@ def tt_search(ctx: Context, best_theta=None, best_S=None, stream=None):
     return best_theta, best_S, int(n.value)
 
 
+def tt_ens_search(ctx: Context, np_f: int = 5, ng_f: int = 1, np_bf: int = 5, ng_bf: int = 1,
+                  n_skip: int = 2, n_cycle: int = 1, n_bucket: int = 64, best_theta=None,
+                  best_S=None, stream=None):
+    """ENS sweep mode; returns (best_theta [n_dom, D], best_S [n_dom], n_evals)."""
+    e = L.EnsCfg(int(np_f), int(ng_f), int(np_bf), int(ng_bf), int(n_skip), int(n_cycle),
+                 int(n_bucket), 0)
+    if best_theta is None:
+        best_theta = torch.empty((ctx.n_dom, ctx.D), dtype=torch.float32, device=ctx.device)
+    if best_S is None:
+        best_S = torch.empty((ctx.n_dom,), dtype=torch.float32, device=ctx.device)
+    n = C.c_uint64(0)
+    _check(ctx.lib, ctx.handle, ctx.lib.tt_ens_search(
+        ctx.handle, C.byref(e), _ptr(best_theta, "best_theta", shape=(ctx.n_dom, ctx.D)),
+        _ptr(best_S, "best_S", shape=(ctx.n_dom,)), C.byref(n), _stream(stream)))
+    return best_theta, best_S, int(n.value)
+
+
 _KERNELS = {"packed": L.TT_KERNEL_PACKED, "persistent": L.TT_KERNEL_PERSISTENT,
             "scalar": L.TT_KERNEL_SCALAR}
 
