@@ -20,6 +20,8 @@ exchange   Neighbour exchange of best individuals between adjacent domains.
 search     The whole search (DE + exchange + gradient polish).
 ens        Evolution by neighborhood similarity in sweep mode (forward
            exploration, backward-and-forward cycles, N_skip interpolation).
+stack      Stacked zero-offset output along an operator (mean centre
+           amplitude over the aperture).
 counts     Semblance-call counts of JADE (eq. jade_semblance) and ENS
            (eq. ens_semblance).
 
@@ -27,4 +29,4 @@ Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, hand-worked fixtures, known-answer vectors, brute force,
 finite differences); none is "parity unpinned".
 """
-from . import semblance, philox, de, exchange, search, counts, ens  # noqa: F401
+from . import semblance, philox, de, exchange, search, counts, ens, stack  # noqa: F401

@@ -28,7 +28,7 @@ def load_worked(path):
             cases.append(cur)
         elif key == "op":
             cur["op"] = CMP if vals[0] == "CMP" else CRS
-        elif key in ("dt", "m0", "expect"):
+        elif key in ("dt", "m0", "expect", "stack"):
             cur[key] = float(vals[0])
         elif key in ("w", "it0"):
             cur[key] = int(vals[0])
