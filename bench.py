@@ -110,6 +110,51 @@ def recovery(wl, best_theta, tol=0.01):
     return {"within_1pct": hits, "of": tried}
 
 
+# ------------------------------------------------------------------ paper comparison
+
+def paper_compare(tt, wl, dev, stream):
+    """The paper's own experiment (Sec. 5.2-5.3, Fig. rms_coherence and
+    ens_jade_execution_time) on this line: JADE (the plain search, no
+    exchange or polish) at 5x1, 30x30 and 80x80 against the ENS sweep at 5x1
+    and 80x80 (NP_bf 5, NG_bf 1, N_skip 2, N_cycle 1, buckets of 64 traces).
+    Each search runs once untimed (graph capture) and once timed; quality is
+    the RMS of the coherence panel (the paper's g-type measure) and the
+    recovery of event-centred parameters."""
+    import copy
+    import torch
+    out = {}
+    for label, kind, npop, ngen in (("jade_5x1", "jade", 5, 1), ("jade_30x30", "jade", 30, 30),
+                                    ("jade_80x80", "jade", 80, 80), ("ens_5x1", "ens", 5, 1),
+                                    ("ens_80x80", "ens", 80, 80)):
+        de = copy.copy(wl.de)
+        de.np, de.ng, de.exch_every, de.polish_steps = max(npop, 5), ngen, 0, 0
+        ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, wl.problem, de, device=dev)
+
+        def run():
+            if kind == "jade":
+                return tt.tt_search(ctx)
+            return tt.tt_ens_search(ctx, npop, ngen, 5, 1, 2, 1, 64)
+
+        run()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        th, S, n = run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        secs = a.elapsed_time(b) / 1e3
+        S = S.cpu().numpy().astype(np.float64)
+        out[label] = {"seconds": secs, "zo_samples_per_s": wl.problem.n_dom / secs,
+                      "calls_per_sample": n / wl.problem.n_dom,
+                      "rms_coherence": float(np.sqrt(np.mean(S * S))),
+                      "recovery": recovery(wl, th.cpu().numpy())}
+        ctx.close()
+    out["jade_30x30_over_ens_5x1_time"] = out["jade_30x30"]["seconds"] / out["ens_5x1"]["seconds"]
+    out["jade_80x80_over_ens_80x80_time"] = (out["jade_80x80"]["seconds"] /
+                                             out["ens_80x80"]["seconds"])
+    return out
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -213,6 +258,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-FP32 and BF16-stored comparison searches")
+    ap.add_argument("--no-paper-compare", action="store_true",
+                    help="skip the ENS-vs-JADE comparison of the paper's experiment")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--cmps", type=int, default=0,
                     help="solve only the first CMPS midpoints of the line (profiling case)")
@@ -362,6 +409,8 @@ def main():
         one_form("bf16_stored", "bf16", "packed", wl.de.polish_steps,
                  "BF16 trace copy, FP32 arithmetic, FP64 chunked energy, polish")
         comparison["speedup_vs_plain_fp32"] = value / comparison["plain_fp32"]["value"]
+        if not args.no_paper_compare:
+            comparison["paper_ens_vs_jade"] = paper_compare(tt, wl, dev, stream)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,

@@ -152,6 +152,21 @@ tt_status tt_semblance_eval(tt_ctx* ctx, const float* theta, int32_t P, float* S
 tt_status tt_semblance_grad(tt_ctx* ctx, const float* theta, int32_t P, float* S, float* dS,
                             void* stream);
 
+/* Stacked zero-offset output along one operator per domain: the output
+ * sample at (m0, t0) is the mean, over the domain's N aperture traces, of the
+ * amplitude at the operator's traveltime, read by the same clamped linear
+ * interpolation as the centre sample of the semblance window:
+ *   out[d] = (1/N) sum_i ((1-f_i) x_i[j_i] + f_i x_i[j_i+1]),
+ * a trace with T < 0 or past the record adding 0, and out[d] = 0 when N = 0.
+ * This is the enhanced zero-offset sample that the operator rebuilds (Sec.
+ * 1) and the stacking panels of Sec. 5.1 show, taken at the searched
+ * parameters. theta [n_dom][D] (device, e.g. tt_search's best_theta), out
+ * [n_dom] (device), both owned by the caller; FP32 with a fixed summation
+ * order (per-lane strided sums, then a butterfly across the warp), so a
+ * call's result does not depend on the launch. Errors: TT_ERR_INVALID_ARG
+ * for NULL arrays. */
+tt_status tt_stack(tt_ctx* ctx, const float* theta, float* out, void* stream);
+
 /* One differential-evolution step per domain (Sec. 2.1.1-2.1.4, p = 1):
  *  gen == 0:  initialise pop [n_dom][NP][D] uniformly in [lo, hi]; other
  *             arrays are ignored and may be NULL.
@@ -257,8 +272,19 @@ tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
  *  TT_OPT_SEARCH_GRAPH  1 (default): tt_search captures its whole launch
  *                 sequence into a CUDA graph on first use and replays it;
  *                 0: launch eagerly. Searches run eagerly while profiling is
- *                 enabled. Changing an option drops a captured graph. */
-enum { TT_OPT_KERNEL = 1, TT_OPT_BLOCK = 2, TT_OPT_SEARCH_GRAPH = 3 };
+ *                 enabled.
+ *  TT_OPT_SPLIT   1 (default): a forward evaluation of fewer than
+ *                 TT_SPLIT_MAX_PAIRS (domain, vector) pairs -- too few to fill
+ *                 the GPU at one warp per 64 pairs -- runs a kernel in which
+ *                 the 8 warps of a block share 64 pairs, each warp summing a
+ *                 contiguous eighth of every pair's aperture, the eight partial
+ *                 sums added in order; every variant then launches that kernel,
+ *                 so S still does not depend on TT_OPT_KERNEL / TT_OPT_BLOCK,
+ *                 but its rounding differs from the unsplit kernels' (both stay
+ *                 within 1e-5 of the exact semblance). 0: never split.
+ *  Changing an option drops a captured graph. */
+enum { TT_OPT_KERNEL = 1, TT_OPT_BLOCK = 2, TT_OPT_SEARCH_GRAPH = 3, TT_OPT_SPLIT = 4 };
+#define TT_SPLIT_MAX_PAIRS (152 * 8 * 64)
 enum { TT_KERNEL_PACKED = 1, TT_KERNEL_PERSISTENT = 2, TT_KERNEL_SCALAR = 3 };
 #define TT_N_TUNE_CANDIDATES 6
 tt_status tt_ctx_set_option(tt_ctx* ctx, int32_t option, int64_t value);

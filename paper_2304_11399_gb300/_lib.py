@@ -10,7 +10,8 @@ LIB_PATH = os.path.join(PKG, "libtt.so")
 TT_OK, TT_ERR_INVALID_ARG, TT_ERR_CUDA, TT_ERR_OUT_OF_MEMORY, TT_ERR_TIMEOUT, \
     TT_ERR_UNSUPPORTED = range(6)
 TT_OP_CMP, TT_OP_CRS = 0, 1
-TT_OPT_KERNEL, TT_OPT_BLOCK, TT_OPT_SEARCH_GRAPH = 1, 2, 3
+TT_OPT_KERNEL, TT_OPT_BLOCK, TT_OPT_SEARCH_GRAPH, TT_OPT_SPLIT = 1, 2, 3, 4
+TT_SPLIT_MAX_PAIRS = 152 * 8 * 64
 TT_KERNEL_PACKED, TT_KERNEL_PERSISTENT, TT_KERNEL_SCALAR = 1, 2, 3
 TT_N_TUNE_CANDIDATES = 6
 TUNE_CANDIDATES = [("packed", 256), ("packed", 128), ("persistent", 256), ("persistent", 128),
@@ -66,6 +67,7 @@ SIGNATURES = {
     "tt_ctx_destroy": (None, [P]),
     "tt_semblance_eval": (I32, [P, P, I32, P, P]),
     "tt_semblance_grad": (I32, [P, P, I32, P, P, P]),
+    "tt_stack": (I32, [P, P, P, P]),
     "tt_de_step": (I32, [P, I32, P, P, P, P, P, P, P]),
     "tt_best_snapshot": (I32, [P, P, P, P, P, P]),
     "tt_neighbor_exchange": (I32, [P, I32, I32, P, P, P, P, P, P]),

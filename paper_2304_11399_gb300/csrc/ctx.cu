@@ -59,6 +59,7 @@ tt::EvalArgs tt_ctx::eval_args(const float* theta, int P, float* S) const {
   a.dom_map = nullptr;
   a.kernel = kernel;
   a.block = block;
+  a.split = split ? 1 : 0;
   a.queue = queue;
   return a;
 }
@@ -90,6 +91,9 @@ extern "C" tt_status tt_ctx_set_option(tt_ctx* c, int32_t option, int64_t value)
     case TT_OPT_SEARCH_GRAPH:
       c->use_graph = value != 0;
       break;
+    case TT_OPT_SPLIT:
+      c->split = value != 0;
+      break;
     default:
       return tt_fail(c, TT_ERR_INVALID_ARG, "unknown option %d", option);
   }
@@ -103,6 +107,7 @@ extern "C" tt_status tt_ctx_get_option(const tt_ctx* c, int32_t option, int64_t*
     case TT_OPT_KERNEL: *value = c->kernel; return TT_OK;
     case TT_OPT_BLOCK: *value = c->block; return TT_OK;
     case TT_OPT_SEARCH_GRAPH: *value = c->use_graph ? 1 : 0; return TT_OK;
+    case TT_OPT_SPLIT: *value = c->split ? 1 : 0; return TT_OK;
   }
   return tt_fail(nullptr, TT_ERR_INVALID_ARG, "unknown option %d", option);
 }

@@ -185,18 +185,16 @@ __device__ __forceinline__ void store_S(const EvalArgs& a, long long q, int d, f
   }
 }
 
-// Scalar evaluation of one (domain, individual) pair over its aperture.
+// Accumulate one pair over aperture entries [r0, r1): the stack sums s_k and
+// the energy -- one FP32 sum over the range (FP32 storage), or the FP64 sum
+// of FP32 sums over 32-entry chunks from r0 (BF16 storage).
 template <int OP, int W, typename T, bool MV>
-__device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
+__device__ __forceinline__ void acc_scalar(const EvalArgs& a, const Lane& L, int r0, int r1,
+                                           float* s, float& E, double& Ed) {
   constexpr int K = 2 * W + 1;
   const T* __restrict__ tr = static_cast<const T*>(a.traces);
-  float s[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) s[k] = 0.f;
-  double Ed = 0.0;  // FP64 sum of per-chunk energies (BF16 storage only)
-  float E = 0.f;
-  for (int c0 = L.e0, c1; c0 < L.e1; c0 = c1) {
-    c1 = (L.e1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : L.e1;
+  for (int c0 = r0, c1; c0 < r1; c0 = c1) {
+    c1 = (r1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : r1;
     float Ec = 0.f;
     for (int e = c0; e < c1; ++e) {
       const float4 t4 = __ldg(a.ap_tab + e);
@@ -214,32 +212,17 @@ __device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
     }
     if (Chunk<T>::kF64) Ed += double(Ec); else E = Ec;
   }
-  float Q = 0.f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
-  return normalise<T>(Q, L.e1 - L.e0, E, Ed);
 }
 
-// One 64-pair unit: each thread evaluates pairs q and q + 32 (either may be
-// absent: past the end, or a domain the map skips). When both lie in one
-// group (the common case: same aperture, possibly different t0) the
-// aperture is walked once and the two windows are processed with packed
-// FP32x2 arithmetic: sample k of the two pairs forms one register pair, so
-// every interpolation, stack and energy update is one f32x2 instruction for
-// both. Otherwise (a group boundary inside the warp, or no second pair) each
-// pair is evaluated on its own (same operations, same bits).
+// The same for two pairs sharing an aperture, with packed FP32x2 arithmetic:
+// sample k of the two pairs forms one register pair, so every interpolation,
+// stack and energy update is one f32x2 instruction for both (same operations
+// and bits as two acc_scalar calls).
 template <int OP, int W, typename T, bool MV>
-__device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int lane) {
+__device__ __forceinline__ void acc_packed(const EvalArgs& a, const Lane& L0, const Lane& L1,
+                                           int r0, int r1, float2* s, float2& E, double& Ed0,
+                                           double& Ed1) {
   constexpr int K = 2 * W + 1;
-  const long long q0 = unit * 64 + lane, q1 = q0 + 32;
-  Lane L0, L1;
-  const bool v0 = lane_setup<OP>(a, q0, L0);
-  const bool v1 = lane_setup<OP>(a, q1, L1);
-  if (!v0 || !v1 || L1.e0 != L0.e0 || L1.e1 != L0.e1 || L1.inv_dt != L0.inv_dt) {
-    if (v0) store_S(a, q0, L0.d, eval_scalar<OP, W, T, MV>(a, L0));
-    if (v1) store_S(a, q1, L1.d, eval_scalar<OP, W, T, MV>(a, L1));
-    return;
-  }
   const T* __restrict__ tr = static_cast<const T*>(a.traces);
   const float2 ca = make_float2(L0.ca, L1.ca), cb = make_float2(L0.cb, L1.cb),
                cc = make_float2(L0.cc, L1.cc), two_p0 = make_float2(L0.two_p0, L1.two_p0),
@@ -248,13 +231,8 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
   const float2 p0p0 = __fmul2_rn(p0v, p0v);
   const float2 m1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f),
                mhalf = make_float2(-0.5f, -0.5f);
-  float2 s[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) s[k] = make_float2(0.f, 0.f);
-  float2 E = make_float2(0.f, 0.f);
-  double Ed0 = 0.0, Ed1 = 0.0;  // FP64 chunk sums (BF16 storage only)
-  for (int c0 = L0.e0, c1; c0 < L0.e1; c0 = c1) {
-    c1 = (L0.e1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : L0.e1;
+  for (int c0 = r0, c1; c0 < r1; c0 = c1) {
+    c1 = (r1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : r1;
     float2 Ec = make_float2(0.f, 0.f);
     for (int e = c0; e < c1; ++e) {
       const float4 t4 = __ldg(a.ap_tab + e);
@@ -318,12 +296,142 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
       E = Ec;
     }
   }
+}
+
+// Scalar evaluation of one (domain, individual) pair over its aperture.
+template <int OP, int W, typename T, bool MV>
+__device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
+  constexpr int K = 2 * W + 1;
+  float s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = 0.f;
+  float E = 0.f;
+  double Ed = 0.0;
+  acc_scalar<OP, W, T, MV>(a, L, L.e0, L.e1, s, E, Ed);
+  float Q = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
+  return normalise<T>(Q, L.e1 - L.e0, E, Ed);
+}
+
+__device__ __forceinline__ bool same_aperture(const Lane& L0, const Lane& L1) {
+  return L1.e0 == L0.e0 && L1.e1 == L0.e1 && L1.inv_dt == L0.inv_dt;
+}
+
+// One 64-pair unit: each thread evaluates pairs q and q + 32 (either may be
+// absent: past the end, or a domain the map skips). When both lie in one
+// group (the common case: same aperture, possibly different t0) the
+// aperture is walked once with packed arithmetic; otherwise each pair is
+// evaluated on its own (same operations, same bits).
+template <int OP, int W, typename T, bool MV>
+__device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int lane) {
+  constexpr int K = 2 * W + 1;
+  const long long q0 = unit * 64 + lane, q1 = q0 + 32;
+  Lane L0, L1;
+  const bool v0 = lane_setup<OP>(a, q0, L0);
+  const bool v1 = lane_setup<OP>(a, q1, L1);
+  if (!v0 || !v1 || !same_aperture(L0, L1)) {
+    if (v0) store_S(a, q0, L0.d, eval_scalar<OP, W, T, MV>(a, L0));
+    if (v1) store_S(a, q1, L1.d, eval_scalar<OP, W, T, MV>(a, L1));
+    return;
+  }
+  float2 s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = make_float2(0.f, 0.f);
+  float2 E = make_float2(0.f, 0.f);
+  double Ed0 = 0.0, Ed1 = 0.0;
+  acc_packed<OP, W, T, MV>(a, L0, L1, L0.e0, L0.e1, s, E, Ed0, Ed1);
   float2 Q = make_float2(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < K; ++k) Q = __ffma2_rn(s[k], s[k], Q);
   const int N = L0.e1 - L0.e0;
   store_S(a, q0, L0.d, normalise<T>(Q.x, N, E.x, Ed0));
   store_S(a, q1, L1.d, normalise<T>(Q.y, N, E.y, Ed1));
+}
+
+// K1 for small launches (few 64-pair units): a block of kSplitWarps warps
+// shares one unit, warp w walking the w-th contiguous slice of every pair's
+// aperture; the slices' partial sums meet in shared memory and are added in
+// slice order. Its summation order (per slice, then across slices) differs
+// from the one-warp-per-unit kernel, so it is chosen by launch size alone --
+// every variant of a small launch runs it -- and results stay reproducible.
+constexpr int kSplitWarps = 8;
+static_assert(TT_SPLIT_MAX_PAIRS % 64 == 0, "split threshold is counted in 64-pair units");
+constexpr long long kSplitMaxUnits = TT_SPLIT_MAX_PAIRS / 64;
+
+template <int OP, int W, typename T, bool MV>
+__global__ void __launch_bounds__(32 * kSplitWarps) k_semblance_split(const EvalArgs a) {
+  constexpr int K = 2 * W + 1;
+  __shared__ float part_s[kSplitWarps][64][K];
+  __shared__ float part_E[kSplitWarps][64];
+  __shared__ double part_Ed[kSplitWarps][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long unit = blockIdx.x;
+  const long long q0 = unit * 64 + lane, q1 = q0 + 32;
+  Lane L0, L1;
+  const bool v0 = lane_setup<OP>(a, q0, L0);
+  const bool v1 = lane_setup<OP>(a, q1, L1);
+  auto slice = [&](const Lane& L, int& r0, int& r1) {
+    const long long n = L.e1 - L.e0;
+    r0 = L.e0 + int(n * w / kSplitWarps);
+    r1 = L.e0 + int(n * (w + 1) / kSplitWarps);
+  };
+  if (v0 && v1 && same_aperture(L0, L1)) {
+    int r0, r1;
+    slice(L0, r0, r1);
+    float2 s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] = make_float2(0.f, 0.f);
+    float2 E = make_float2(0.f, 0.f);
+    double Ed0 = 0.0, Ed1 = 0.0;
+    acc_packed<OP, W, T, MV>(a, L0, L1, r0, r1, s, E, Ed0, Ed1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      part_s[w][lane][k] = s[k].x;
+      part_s[w][lane + 32][k] = s[k].y;
+    }
+    part_E[w][lane] = E.x;
+    part_E[w][lane + 32] = E.y;
+    part_Ed[w][lane] = Ed0;
+    part_Ed[w][lane + 32] = Ed1;
+  } else {
+    for (int h = 0; h < 2; ++h) {
+      const Lane& L = h ? L1 : L0;
+      if (!(h ? v1 : v0)) continue;
+      int r0, r1;
+      slice(L, r0, r1);
+      float s[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k] = 0.f;
+      float E = 0.f;
+      double Ed = 0.0;
+      acc_scalar<OP, W, T, MV>(a, L, r0, r1, s, E, Ed);
+      const int p = lane + 32 * h;
+#pragma unroll
+      for (int k = 0; k < K; ++k) part_s[w][p][k] = s[k];
+      part_E[w][p] = E;
+      part_Ed[w][p] = Ed;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int p = threadIdx.x;
+    Lane L;
+    if (!lane_setup<OP>(a, unit * 64 + p, L)) return;
+    float Q = 0.f, E = 0.f;
+    double Ed = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float sk = 0.f;
+      for (int v = 0; v < kSplitWarps; ++v) sk = __fadd_rn(sk, part_s[v][p][k]);
+      Q = fmaf(sk, sk, Q);
+    }
+    for (int v = 0; v < kSplitWarps; ++v) {
+      E = __fadd_rn(E, part_E[v][p]);
+      Ed += part_Ed[v][p];
+    }
+    store_S(a, unit * 64 + p, L.d, normalise<T>(Q, L.e1 - L.e0, E, Ed));
+  }
 }
 
 // K1, grid-mapped (queue == nullptr: one 64-pair unit per warp, the grid
@@ -435,6 +543,33 @@ __global__ void __launch_bounds__(kBlock) k_semblance_grad(const EvalArgs a) {
 
 using KFn = void (*)(const EvalArgs);
 
+// Stacked output: one warp per domain (P = 1, theta [n_dom][D]); lane l sums
+// the centre amplitudes of aperture entries e0 + l, e0 + l + 32, ... in order,
+// the 32 lane sums meet in a butterfly, and the mean is one FP32 division.
+// Positions are those of the semblance window's centre sample (same clamp:
+// T < 0 or past the record reads the zero padding).
+template <int OP, typename T, bool MV>
+__global__ void __launch_bounds__(256) k_stack(const EvalArgs a, float* __restrict__ out) {
+  const long long d = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  Lane L;
+  if (!lane_setup<OP>(a, d, L)) return;  // warp-uniform: the whole warp leaves
+  const T* __restrict__ tr = static_cast<const T*>(a.traces);
+  float s = 0.f;
+  for (int e = L.e0 + lane; e < L.e1; e += 32) {
+    const float4 t4 = __ldg(a.ap_tab + e);
+    const Pos P = locate<OP, MV>(L, t4);
+    const T* x = tr + (__float_as_uint(t4.w) + P.j);
+    s = __fadd_rn(s, fmaf(P.f, ld_sample<T>(x + 1), __fmul_rn(P.g, ld_sample<T>(x))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if (lane == 0) {
+    const int N = L.e1 - L.e0;
+    out[L.d] = N > 0 ? __fdiv_rn(s, float(N)) : 0.f;
+  }
+}
+
 constexpr int kDirectMax = 2048;  // direct position up to u = 2048 samples
 
 #define TT_W_TABLE(NAME)                                                                  \
@@ -468,6 +603,7 @@ constexpr int kDirectMax = 2048;  // direct position up to u = 2048 samples
 
 TT_W_TABLE(k_semblance)
 TT_W_TABLE(k_semblance_scalar)
+TT_W_TABLE(k_semblance_split)
 TT_W_TABLE(k_semblance_grad)
 #undef TT_W_TABLE
 
@@ -483,6 +619,12 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
   if (grad) {
     fn = k_semblance_grad_select(a.op, a.storage, a.W, mv);
     blocks = (n + block - 1) / block;
+  } else if (a.split && (n + 63) / 64 < kSplitMaxUnits) {
+    // few units: a block per unit, the aperture split over its warps
+    fn = k_semblance_split_select(a.op, a.storage, a.W, mv);
+    if (!fn) return cudaErrorInvalidValue;
+    fn<<<unsigned((n + 63) / 64), 32 * kSplitWarps, 0, s>>>(b);
+    return cudaGetLastError();
   } else if (a.kernel == TT_KERNEL_SCALAR) {
     fn = k_semblance_scalar_select(a.op, a.storage, a.W, mv);
     blocks = (n + block - 1) / block;
@@ -513,6 +655,25 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
 }  // namespace
 
 cudaError_t launch_semblance(const EvalArgs& a, cudaStream_t s) { return launch(a, s, false); }
+
+cudaError_t launch_stack(const EvalArgs& a, float* out, cudaStream_t s) {
+  if (a.n_dom == 0) return cudaSuccess;
+  if (a.P != 1) return cudaErrorInvalidValue;
+  const bool mv = a.umax > float(kDirectMax);
+  using SFn = void (*)(const EvalArgs, float*);
+  SFn fn = nullptr;
+  const bool bf = a.storage == TT_STORE_BF16;
+  if (a.op == TT_OP_CMP)
+    fn = bf ? (mv ? k_stack<TT_OP_CMP, __nv_bfloat16, true> : k_stack<TT_OP_CMP, __nv_bfloat16, false>)
+            : (mv ? k_stack<TT_OP_CMP, float, true> : k_stack<TT_OP_CMP, float, false>);
+  else
+    fn = bf ? (mv ? k_stack<TT_OP_CRS, __nv_bfloat16, true> : k_stack<TT_OP_CRS, __nv_bfloat16, false>)
+            : (mv ? k_stack<TT_OP_CRS, float, true> : k_stack<TT_OP_CRS, float, false>);
+  const long long blocks = ((long long)a.n_dom * 32 + 255) / 256;
+  if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+  fn<<<unsigned(blocks), 256, 0, s>>>(a, out);
+  return cudaGetLastError();
+}
 cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s) { return launch(a, s, true); }
 
 }  // namespace tt
@@ -525,6 +686,14 @@ extern "C" tt_status tt_semblance_eval(tt_ctx* ctx, const float* theta, int32_t 
   tt::EvalArgs a = ctx->eval_args(theta, P, S);
   return tt_cuda_check(ctx, ctx->semblance(a, static_cast<cudaStream_t>(stream), false),
                        "semblance launch");
+}
+
+extern "C" tt_status tt_stack(tt_ctx* ctx, const float* theta, float* out, void* stream) {
+  if (!ctx) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->n_dom > 0 && (!theta || !out)) return tt_fail(ctx, TT_ERR_INVALID_ARG, "NULL array");
+  tt::EvalArgs a = ctx->eval_args(theta, 1, nullptr);
+  return tt_cuda_check(ctx, ctx->counted(tt::launch_stack(a, out, static_cast<cudaStream_t>(stream))),
+                       "stack launch");
 }
 
 extern "C" tt_status tt_semblance_grad(tt_ctx* ctx, const float* theta, int32_t P, float* S,

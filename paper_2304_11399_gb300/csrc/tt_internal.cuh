@@ -39,11 +39,13 @@ struct EvalArgs {
   const int* dom_map;       // optional: local domain r -> global domain (-1: skip r)
   int kernel;               // TT_KERNEL_PACKED / _PERSISTENT / _SCALAR (forward launches)
   int block;                // threads per block: 128 or 256
+  int split;                // 1: small forward launches split the aperture over warps
   unsigned long long* queue;  // persistent mode: work-unit counter, zero at launch
 };
 
 cudaError_t launch_semblance(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s);
+cudaError_t launch_stack(const EvalArgs& a, float* out, cudaStream_t s);
 
 struct DeArgs {
   int n_dom, NP, D, gen;
@@ -162,6 +164,7 @@ struct tt_ctx {
   unsigned long long* queue = nullptr;  // persistent-kernel work counter
   // launch configuration (tt_ctx_set_option / tt_ctx_autotune)
   int kernel = TT_KERNEL_PACKED, block = 256;
+  bool split = true;  // TT_OPT_SPLIT
   bool use_graph = true;
   // CUDA graph of the whole search, captured on first use
   cudaStream_t cap_stream = nullptr;

@@ -156,6 +156,20 @@ def tt_semblance_eval(ctx: Context, theta: torch.Tensor, S: torch.Tensor | None 
     return S
 
 
+def tt_stack(ctx: Context, theta: torch.Tensor, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    """Stacked zero-offset sample out [n_dom] along theta [n_dom, D] (one
+    operator per domain, e.g. the best theta of a search)."""
+    if theta.dim() == 3 and theta.shape[1] == 1:
+        theta = theta[:, 0]
+    tp = _ptr(theta, "theta", shape=(ctx.n_dom, ctx.D))
+    if out is None:
+        out = torch.empty((ctx.n_dom,), dtype=torch.float32, device=theta.device)
+    op = _ptr(out, "out", shape=(ctx.n_dom,))
+    _check(ctx.lib, ctx.handle, ctx.lib.tt_stack(ctx.handle, tp, op, _stream(stream)))
+    return out
+
+
 def tt_semblance_grad(ctx: Context, theta: torch.Tensor, stream=None):
     """(S [n_dom, P], dS/dtheta [n_dom, P, D]) for theta [n_dom, P, D]."""
     P = int(theta.shape[1])
@@ -249,14 +263,17 @@ _KERNELS = {"packed": L.TT_KERNEL_PACKED, "persistent": L.TT_KERNEL_PERSISTENT,
 
 
 def tt_ctx_set_option(ctx: Context, option: str, value):
-    """option: "kernel" ("packed" | "persistent" | "scalar"), "block" (128 | 256)
-    or "search_graph" (bool)."""
+    """option: "kernel" ("packed" | "persistent" | "scalar"), "block" (128 | 256),
+    "search_graph" (bool) or "split" (bool: split the aperture over the warps
+    of a block for launches of fewer than TT_SPLIT_MAX_PAIRS pairs)."""
     if option == "kernel":
         code, v = L.TT_OPT_KERNEL, _KERNELS[value]
     elif option == "block":
         code, v = L.TT_OPT_BLOCK, int(value)
     elif option == "search_graph":
         code, v = L.TT_OPT_SEARCH_GRAPH, 1 if value else 0
+    elif option == "split":
+        code, v = L.TT_OPT_SPLIT, 1 if value else 0
     else:
         raise ValueError(f"unknown option {option}")
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_set_option(ctx.handle, code, v))
@@ -264,12 +281,12 @@ def tt_ctx_set_option(ctx: Context, option: str, value):
 
 def tt_ctx_get_option(ctx: Context, option: str):
     code = {"kernel": L.TT_OPT_KERNEL, "block": L.TT_OPT_BLOCK,
-            "search_graph": L.TT_OPT_SEARCH_GRAPH}[option]
+            "search_graph": L.TT_OPT_SEARCH_GRAPH, "split": L.TT_OPT_SPLIT}[option]
     v = C.c_int64()
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_get_option(ctx.handle, code, C.byref(v)))
     if option == "kernel":
         return {b: a for a, b in _KERNELS.items()}[v.value]
-    return bool(v.value) if option == "search_graph" else int(v.value)
+    return bool(v.value) if option in ("search_graph", "split") else int(v.value)
 
 
 def tt_ctx_autotune(ctx: Context, theta: torch.Tensor, stream=None):

@@ -5,8 +5,9 @@ Packed problems: many independent CRS problems with 16-240 traces and
 750-3000 samples at 2 or 4 ms each, in one context and one launch per
 generation. Every semblance kernel variant (packed grid, persistent queue,
 scalar; 128 or 256 threads) performs the same operations in the same order,
-so they must agree bit for bit; the graph-replayed search must equal the
-eagerly launched one bit for bit.
+so they must agree bit for bit; small launches run the aperture-split kernel
+under every variant (bit for bit the same again, within 1e-5 of the oracle);
+the graph-replayed search must equal the eagerly launched one bit for bit.
 """
 import numpy as np
 import pytest
@@ -22,13 +23,26 @@ VARIANTS = _lib.TUNE_CANDIDATES
 
 
 def _all_variants(ctx, theta):
-    out = {}
+    """S from the six one-warp-per-unit variants (split off) and, under key
+    "split", from the aperture-split small-launch kernel of every variant."""
+    out, split = {}, []
     for kern, block in VARIANTS:
         tt.tt_ctx_set_option(ctx, "kernel", kern)
         tt.tt_ctx_set_option(ctx, "block", block)
+        tt.tt_ctx_set_option(ctx, "split", False)
         out[(kern, block)] = tt.tt_semblance_eval(ctx, theta).cpu().numpy()
+        tt.tt_ctx_set_option(ctx, "split", True)
+        split.append(tt.tt_semblance_eval(ctx, theta).cpu().numpy())
     tt.tt_ctx_set_option(ctx, "kernel", "packed")
     tt.tt_ctx_set_option(ctx, "block", 256)
+    n_pairs = split[0].size
+    if n_pairs < _lib.TT_SPLIT_MAX_PAIRS:
+        for v in split[1:]:
+            assert np.array_equal(v, split[0])
+    else:  # too many pairs to split: the option changes nothing
+        for k, v in zip(VARIANTS, split):
+            assert np.array_equal(v, out[k])
+    out["split"] = split[0]
     return out
 
 
@@ -48,9 +62,10 @@ def test_variants_bit_identical_on_a_line(P):
         res = _all_variants(ctx, to_dev(theta))
         ctx.close()
         ref = res[("packed", 256)]
-        for k, v in res.items():
-            assert np.array_equal(v, ref), (storage, k)
+        for k in VARIANTS:
+            assert np.array_equal(res[k], ref), (storage, k)
         assert np.max(np.abs(ref - ora)) <= tol
+        assert np.max(np.abs(res["split"] - ora)) <= tol
 
 
 def test_batched_uneven_parity_all_variants(batch):
@@ -60,15 +75,16 @@ def test_batched_uneven_parity_all_variants(batch):
     ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, device=dev())
     res = _all_variants(ctx, to_dev(theta))
     ref = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, prob, theta)
-    for k, v in res.items():
-        assert np.array_equal(v, res[("packed", 256)]), k
+    for k in VARIANTS:
+        assert np.array_equal(res[k], res[("packed", 256)]), k
     assert np.max(np.abs(res[("packed", 256)] - ref)) <= 1e-5
+    assert np.max(np.abs(res["split"] - ref)) <= 1e-5
     times = tt.tt_ctx_autotune(ctx, to_dev(theta))
     assert set(times) == set(VARIANTS) and all(t > 0 for t in times.values())
     best = min(times, key=times.get)
     assert (tt.tt_ctx_get_option(ctx, "kernel"), tt.tt_ctx_get_option(ctx, "block")) == best
     S = tt.tt_semblance_eval(ctx, to_dev(theta)).cpu().numpy()
-    assert np.array_equal(S, res[("packed", 256)])
+    assert np.array_equal(S, res["split"])  # a small launch: split by default
     ctx.close()
 
 

@@ -100,7 +100,9 @@ def test_autograd_backward_is_adjoint(points):
     (out * w).sum().backward()
     expect = w.unsqueeze(-1) * to_dev(G).unsqueeze(1)
     torch.testing.assert_close(th.grad, expect, rtol=1e-6, atol=0)
-    np.testing.assert_allclose(out.detach().cpu().numpy()[:, 0], S, rtol=0, atol=1e-7)
+    # the forward is K1 (at 1000 points the aperture-split small-launch
+    # kernel), S is K2's: two FP32 summation orders of the same sums
+    np.testing.assert_allclose(out.detach().cpu().numpy()[:, 0], S, rtol=0, atol=1e-6)
 
 
 def test_cmp_gradient_and_polish():
@@ -126,7 +128,8 @@ def test_cmp_gradient_and_polish():
     S0 = tt.tt_semblance_eval(ctx, th[:, None, :].contiguous()).cpu().numpy()[:, 0]
     th, Sp = tt.tt_polish(ctx, th, 5, wl.de.polish_lr)
     Sp = Sp.cpu().numpy()
-    assert np.all(Sp >= S0 - 1e-7)
+    # iterate 0's S comes from K2, S0 from K1 (two FP32 summation orders)
+    assert np.all(Sp >= S0 - 1e-6)
     ref = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, prob,
                                           th.cpu().numpy()[:, None, :])[:, 0]
     assert np.max(np.abs(ref - Sp)) <= 1e-5
