@@ -16,6 +16,9 @@ philox     Philox4x32-10 counter-based generator (Salmon et al., SC'11).
 de         One differential-evolution generation (init, selection, best,
            DE/current-to-best/1/bin mutation+crossover, bound repair) in FP32,
            the precision the search's integer decisions are taken in.
+jade       JADE's adaptation of F and CR (normal / Cauchy draws around a
+           memory updated from successful children) and its archive of
+           replaced parents, with only correctly rounded float32 operations.
 exchange   Neighbour exchange of best individuals between adjacent domains.
 search     The whole search (DE + exchange + gradient polish).
 ens        Evolution by neighborhood similarity in sweep mode (forward
@@ -29,4 +32,4 @@ Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (closed forms, hand-worked fixtures, known-answer vectors, brute force,
 finite differences); none is "parity unpinned".
 """
-from . import semblance, philox, de, exchange, search, counts, ens, stack  # noqa: F401
+from . import semblance, philox, de, jade, exchange, search, counts, ens, stack  # noqa: F401

@@ -1,8 +1,10 @@
 """The whole traveltime-parameter search (TEST INFRASTRUCTURE).
 
 Per domain (zero-offset sample) the JADE loop of Sec. 2.1 / Fig. 3 with
-p = 1 and fixed F, CR (``oracle.de``), driven over all domains at once with
-the neighbour exchange of Sec. 3.4 (``oracle.exchange``):
+p = 1, with fixed F, CR (``oracle.de``) or, when ``cfg.adapt`` is set, with
+JADE's adaptation of F and CR and its archive (``oracle.jade``), driven over
+all domains at once with the neighbour exchange of Sec. 3.4
+(``oracle.exchange``):
 
     gen 0:          init population, evaluate it
     gen g = 1..NG:  best -> mutate/crossover -> evaluate trial -> select
@@ -27,6 +29,7 @@ import numpy as np
 
 from . import de as de_mod
 from . import exchange as ex
+from . import jade
 from .semblance import semblance_many, domain_data, semblance, semblance_grad
 
 
@@ -52,10 +55,12 @@ def polish_point(x, dt, dm, h, t0, op, w, theta0, lo, hi, steps, lr):
     return best_th, best_S, steps + 1
 
 
-def search(traces, mid, off, prob, cfg, *, history=None):
+def search(traces, mid, off, prob, cfg, *, history=None, jade_states=None):
     """Run the search over every domain of ``prob`` with settings ``cfg``
     (attributes np, ng, F, CR, seed, lo, hi, exch_every, polish_steps,
-    polish_lr). ``history``, if a list, receives the mean best S per gen."""
+    polish_lr and optionally adapt). ``history``, if a list, receives the
+    mean best S per gen; ``jade_states``, if a list, the final adaptation
+    state of every domain."""
     lo = np.asarray(cfg.lo, np.float32)
     hi = np.asarray(cfg.hi, np.float32)
     n_dom, NP, D = prob.n_dom, cfg.np, len(cfg.lo)
@@ -64,13 +69,25 @@ def search(traces, mid, off, prob, cfg, *, history=None):
     fit = _eval(traces, mid, off, prob, pop)
     n_evals = n_dom * NP
     grid = cfg.exch_every > 0 and prob.n_m0 * prob.n_t0 == n_dom and n_dom > 0
+    adapt = bool(getattr(cfg, "adapt", 0))
+    states = [jade.new_state(NP, D, cfg.F, cfg.CR) for _ in range(n_dom)] if adapt else None
     for g in range(1, cfg.ng + 1):
-        pop, fit, trial, _ = de_mod.de_step(g, pop, fit, None, None, cfg.seed, cfg.F, cfg.CR,
-                                            lo, hi)
+        if adapt:
+            trial = np.empty_like(pop)
+            for d in range(n_dom):
+                trial[d], _ = jade.trial_population(states[d], cfg.seed, d, g, pop[d], fit[d],
+                                                    lo, hi)
+        else:
+            pop, fit, trial, _ = de_mod.de_step(g, pop, fit, None, None, cfg.seed, cfg.F,
+                                                cfg.CR, lo, hi)
         tfit = _eval(traces, mid, off, prob, trial)
         n_evals += n_dom * NP
         for d in range(n_dom):
-            pop[d], fit[d] = de_mod.select(pop[d], fit[d], trial[d], tfit[d])
+            if adapt:
+                pop[d], fit[d] = jade.select_adapt(states[d], cfg.seed, d, g, pop[d], fit[d],
+                                                   trial[d], tfit[d])
+            else:
+                pop[d], fit[d] = de_mod.select(pop[d], fit[d], trial[d], tfit[d])
         if grid and g % cfg.exch_every == 0:
             snap = ex.best_snapshot(pop, fit)
             imports, slots = ex.exchange_plan(prob.n_m0, prob.n_t0, pop, fit, snap)
@@ -91,4 +108,6 @@ def search(traces, mid, off, prob, cfg, *, history=None):
                 x, dt, dm, h, t0, prob.op, prob.half_window, best_theta[d], lo, hi,
                 cfg.polish_steps, cfg.polish_lr)
             n_evals += n
+    if adapt and jade_states is not None:
+        jade_states.extend(states)
     return best_theta, best_S, n_evals

@@ -27,6 +27,7 @@ class DEConfig:
     exch_every: int = 0
     polish_steps: int = 0
     polish_lr: float = 0.0
+    adapt: int = 0           # 1: JADE adaptation of F, CR (initial mu = F, CR) + archive
 
     def as_arrays(self):
         return np.asarray(self.lo, np.float32), np.asarray(self.hi, np.float32)
