@@ -114,9 +114,10 @@ def recovery(wl, best_theta, tol=0.01):
 
 def paper_compare(tt, wl, dev, stream):
     """The paper's own experiment (Sec. 5.2-5.3, Fig. rms_coherence and
-    ens_jade_execution_time) on this line: JADE (the plain search, no
-    exchange or polish) at 5x1, 30x30 and 80x80 against the ENS sweep at 5x1
-    and 80x80 (NP_bf 5, NG_bf 1, N_skip 2, N_cycle 1, buckets of 64 traces).
+    ens_jade_execution_time) on this line: JADE (the plain search with the
+    adaptation of F and CR and the archive, mu starting at 0.5, no exchange
+    or polish) at 5x1, 30x30 and 80x80 against the ENS sweep at 5x1 and 80x80
+    (NP_bf 5, NG_bf 1, N_skip 2, N_cycle 1, buckets of 64 traces).
     Each search runs once untimed (graph capture) and once timed; quality is
     the RMS of the coherence panel (the paper's g-type measure) and the
     recovery of event-centred parameters."""
@@ -128,6 +129,8 @@ def paper_compare(tt, wl, dev, stream):
                                     ("ens_80x80", "ens", 80, 80)):
         de = copy.copy(wl.de)
         de.np, de.ng, de.exch_every, de.polish_steps = max(npop, 5), ngen, 0, 0
+        if kind == "jade":
+            de.adapt, de.F, de.CR = 1, 0.5, 0.5
         ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, wl.problem, de, device=dev)
 
         def run():

@@ -95,11 +95,14 @@ typedef struct tt_problem {
                          /* 0, 0 = no grid (no exchange)                     */
 } tt_problem;
 
-/* Search settings (Sec. 2.1: NP, NG; F, CR held fixed; p = 1). */
+/* Search settings (Sec. 2.1: NP, NG, p = 1; F and CR fixed, or adapted as
+ * in JADE when `adapt` is 1). */
 typedef struct tt_de_cfg {
   int32_t np;            /* population size NP, 4..1024                     */
   int32_t ng;            /* generations NG >= 0                             */
-  float F, CR;           /* mutation factor, crossover rate in [0, 1]       */
+  float F, CR;           /* mutation factor in [0, 2], crossover rate in    */
+                         /* [0, 1]; with adapt = 1 the initial mu_F in      */
+                         /* (0, 1] and mu_CR in [0, 1] (JADE: 0.5, 0.5)     */
   uint64_t seed;         /* Philox4x32-10 key                               */
   float lo[TT_MAX_DIM];  /* parameter bounds, lo[d] <= hi[d]                */
   float hi[TT_MAX_DIM];
@@ -107,7 +110,16 @@ typedef struct tt_de_cfg {
                          /* exch_every-th generation; 0 = never             */
   int32_t polish_steps;  /* projected gradient-ascent steps after DE        */
   float polish_lr;       /* step: theta += lr (hi-lo)^2 dS/dtheta           */
-  int32_t reserved;
+  int32_t adapt;         /* 0: fixed F, CR. 1: JADE adaptation (Sec. 2.1.4,  */
+                         /* the cited JADE with c = 0.1): per member        */
+                         /* CR_i ~ N(mu_CR, 0.1) clipped to [0, 1], F_i ~   */
+                         /* Cauchy(mu_F, 0.1) redrawn while <= 0, capped at */
+                         /* 1; r2 drawn from population + archive of the    */
+                         /* parents of strictly better children (<= NP,     */
+                         /* uniform replacement when full); mu moved by c   */
+                         /* towards the mean CR and Lehmer-mean F of the    */
+                         /* successes. tt_search and tt_de_step only (the   */
+                         /* ENS sweep keeps F, CR fixed).                   */
 } tt_de_cfg;
 
 typedef struct tt_ctx tt_ctx;
@@ -177,6 +189,12 @@ tt_status tt_stack(tt_ctx* ctx, const float* theta, float* out, void* stream);
  *             v = x_i + F (x_best - x_i) + F (x_r1 - x_r2), binomial
  *             crossover with j_rand, repair v<lo -> (lo+x_i)/2,
  *             v>hi -> (hi+x_i)/2, written to next_trial [n_dom][NP][D].
+ *  cfg.adapt: the JADE state (mu_CR, mu_F, archive, the trial's F_i and
+ *             CR_i) lives in the context: gen 0 resets it; a selection
+ *             updates the archive and mu (the trial selected is that of
+ *             generation gen - 1 when next_trial != NULL, else of gen);
+ *             the mutation draws F_i, CR_i and takes r2 from population +
+ *             archive. One search per context at a time.
  * Random numbers: Philox4x32-10, key = seed, counter = (i, gen, domain,
  * block); FP32 arithmetic with one rounding per operation, so results are
  * bit-reproducible. pop and fit [n_dom][NP] are updated in place;

@@ -44,7 +44,7 @@ class DECfg(C.Structure):
     _fields_ = [("np", I32), ("ng", I32), ("F", C.c_float), ("CR", C.c_float),
                 ("seed", C.c_uint64), ("lo", C.c_float * TT_MAX_DIM),
                 ("hi", C.c_float * TT_MAX_DIM), ("exch_every", I32), ("polish_steps", I32),
-                ("polish_lr", C.c_float), ("reserved", I32)]
+                ("polish_lr", C.c_float), ("adapt", I32)]
 
 
 class EnsCfg(C.Structure):

@@ -310,7 +310,8 @@ void free_ctx(tt_ctx* c) {
                   c->dom_it0, c->dom_group, c->bounds, c->pop, c->fit, c->trial[0],
                   c->trial[1], c->tfit[0], c->tfit[1], c->snap, c->imports, c->slots,
                   c->best_idx, c->pol_th, c->pol_g, c->pol_S, c->pol_bth, c->pol_bS, c->d_err,
-                  c->queue, c->out_th, c->out_S};
+                  c->queue, c->out_th, c->out_S, c->jade_mu, c->jade_arc, c->jade_F,
+                  c->jade_CR, c->jade_na};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto e : c->ev) cudaEventDestroy(e);
@@ -391,6 +392,12 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
         return tt_fail(nullptr, TT_ERR_INVALID_ARG, "bad bounds in dimension %d", d);
     if (cfg->exch_every < 0 || cfg->polish_steps < 0 || !std::isfinite(cfg->polish_lr))
       return tt_fail(nullptr, TT_ERR_INVALID_ARG, "bad exchange/polish settings");
+    if (cfg->adapt != 0 && cfg->adapt != 1)
+      return tt_fail(nullptr, TT_ERR_INVALID_ARG, "adapt must be 0 or 1");
+    if (cfg->adapt && !(cfg->F > 0.f && cfg->F <= 1.f))
+      return tt_fail(nullptr, TT_ERR_INVALID_ARG, "adaptive search: initial F in (0, 1]");
+    if (cfg->adapt && cfg->ng >= (1 << 30) - 1)
+      return tt_fail(nullptr, TT_ERR_INVALID_ARG, "adaptive search: ng must be below 2^30 - 1");
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tt_ctx* c = new tt_ctx();
@@ -536,6 +543,13 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
     TRY(dalloc(&c->imports, nd * 4 * Dz), "alloc imports");
     TRY(dalloc(&c->slots, nd * 4), "alloc slots");
     TRY(dalloc(&c->best_idx, nd), "alloc best");
+    if (cfg->adapt) {
+      TRY(dalloc(&c->jade_mu, nd * 2), "alloc adaptation");
+      TRY(dalloc(&c->jade_na, nd), "alloc adaptation");
+      TRY(dalloc(&c->jade_arc, nd * np * Dz), "alloc archive");
+      TRY(dalloc(&c->jade_F, nd * np), "alloc adaptation");
+      TRY(dalloc(&c->jade_CR, nd * np), "alloc adaptation");
+    }
   }
   TRY(dalloc(&c->queue, 1), "alloc queue");
   {

@@ -230,6 +230,7 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
         bool pending = false;
         for (int gi = 1; gi <= NG; ++gi) {
           tt::DeArgs a = tt_make_de_args(c, int(gen0) + gi);
+          a.adapt = 0;  // the sweep's short evolutions keep F and CR fixed
           a.n_dom = n_est_loc;
           a.NP = NP;
           a.dom_map = map_est;
@@ -249,6 +250,7 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
         }
         if (pending) {
           tt::DeArgs a = tt_make_de_args(c, int(gen0) + NG + 1);
+          a.adapt = 0;
           a.n_dom = n_est_loc;
           a.NP = NP;
           a.dom_map = map_est;

@@ -106,6 +106,7 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
     cur ^= 1;
     if (grid && g % cfg.exch_every == 0) {
       a = tt_make_de_args(c, g);
+      a.sel_gen = g;  // select-only: the trial of this generation
       a.pop = c->pop;
       a.fit = c->fit;
       a.trial = c->trial[cur ^ 1];
@@ -127,6 +128,7 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
   }
   if (pending) {
     a = tt_make_de_args(c, NG + 1);
+    a.sel_gen = NG;  // select-only: the last trial
     a.pop = c->pop;
     a.fit = c->fit;
     a.trial = c->trial[cur ^ 1];

@@ -60,6 +60,15 @@ struct DeArgs {
   float F;
   uint32_t cr_thr;          // floor(CR * 2^24)
   float lo[TT_MAX_DIM], hi[TT_MAX_DIM];
+  // JADE adaptation (adapt == 1): per-domain state indexed like pop
+  int adapt;
+  int sel_gen;              // generation of the trial being selected
+  float CR0;                // initial mu_CR (the initial mu_F is F)
+  float* jade_mu;           // [n_dom][2]: mu_CR, mu_F
+  int* jade_na;             // [n_dom] archive fill
+  float* jade_arc;          // [n_dom][NP][D] archived parents
+  float* jade_F;            // [n_dom][NP] F_i of the pending trial
+  float* jade_CR;           // [n_dom][NP] CR_i of the pending trial
 };
 
 cudaError_t launch_de_step(const DeArgs& a, cudaStream_t s);
@@ -158,6 +167,8 @@ struct tt_ctx {
   float* tfit[2] = {nullptr, nullptr};
   float *snap = nullptr, *imports = nullptr;
   int *slots = nullptr, *best_idx = nullptr;
+  float *jade_mu = nullptr, *jade_arc = nullptr, *jade_F = nullptr, *jade_CR = nullptr;
+  int* jade_na = nullptr;
   float *pol_th = nullptr, *pol_g = nullptr, *pol_S = nullptr, *pol_bth = nullptr,
         *pol_bS = nullptr;
   int* d_err = nullptr;     // device-side validation flag

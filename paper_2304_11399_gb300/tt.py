@@ -120,6 +120,7 @@ def tt_ctx_create(traces, mid, off, problem, cfg=None, *, storage: str = "f32",
         c.exch_every = int(getattr(cfg, "exch_every", 0))
         c.polish_steps = int(getattr(cfg, "polish_steps", 0))
         c.polish_lr = float(getattr(cfg, "polish_lr", 0.0))
+        c.adapt = int(getattr(cfg, "adapt", 0))
         cfg_p = C.byref(c)
         npop = c.np
     h = C.c_void_p()
