@@ -11,6 +11,16 @@ maps into [0, 1]. The readings adopted here:
     CMP  (theta = C):        T = t0^2 + C h^2
     CRS  (theta = A, B, C):  T = (t0 + A dm)^2 + B dm^2 + C h^2
   t = sqrt(T); where T < 0 the trace contributes zeros (it still counts in N).
+* FO-CRS (Sec. 1: two slopes and three wavefront curvatures; the hyperbolic
+  finite-offset CRS operator of the cited Zhang et al. 2001), for the sample
+  t0 of a common-offset section at central full offset h0, with
+  dh = h - h0 (the ``h`` argument of the functions below is then dh):
+    FO-CRS (theta = Am, Ah, Bmm, Bmh, Bhh):
+      T = (t0 + Am dm + Ah dh)^2 + Bmm dm^2 + Bmh dm dh + Bhh dh^2,
+  the second-order (hyperbolic) expansion of t^2 in the midpoint and offset
+  displacements; its physical parameters (emergence angles, curvatures) are
+  absorbed into the five coefficients, as the CRS constants are into A, B, C.
+  With h0 = 0, Ah = 0, Bmh = 0 and Bhh = C it is the CRS operator.
 * Window: the 2w+1 samples at t + k dt, k = -w..w, read by linear
   interpolation: with u = t/dt, j = floor(u), f = u - j,
     a_k = (1 - f) x[j + k] + f x[j + k + 1],   x[n] = 0 outside [0, NT-1].
@@ -24,7 +34,7 @@ from __future__ import annotations
 
 import numpy as np
 
-CMP, CRS = 0, 1
+CMP, CRS, FOCRS = 0, 1, 2
 
 
 def traveltime_sq(op: int, theta, t0, dm, h):
@@ -34,6 +44,10 @@ def traveltime_sq(op: int, theta, t0, dm, h):
     if op == CMP:
         (C,) = (float(v) for v in theta)
         return t0 * t0 + C * h * h
+    if op == FOCRS:
+        Am, Ah, Bmm, Bmh, Bhh = (float(v) for v in theta)
+        dh = h
+        return (t0 + Am * dm + Ah * dh) ** 2 + Bmm * dm * dm + Bmh * dm * dh + Bhh * dh * dh
     A, B, C = (float(v) for v in theta)
     return (t0 + A * dm) ** 2 + B * dm * dm + C * h * h
 
@@ -94,13 +108,15 @@ def semblance_grad(x, dt, dm, h, t0, op, theta, w):
     With Q = sum_k s_k^2, dS/da_ik = 2 s_k / (N E) - 2 S a_ik / E; inside an
     interpolation cell da_ik/du_i = x[j+k+1] - x[j+k]; du/dtheta =
     (dT/dtheta) / (2 t dt) with dT/dA = 2 (t0 + A dm) dm, dT/dB = dm^2,
-    dT/dC = h^2 (CMP: only dT/dC). Traces with T < 0, or t = 0, add nothing;
-    E = 0 gives S = 0 and a zero gradient.
+    dT/dC = h^2 (CMP: only dT/dC); FO-CRS, with q = t0 + Am dm + Ah dh:
+    dT/dAm = 2 q dm, dT/dAh = 2 q dh, dT/dBmm = dm^2, dT/dBmh = dm dh,
+    dT/dBhh = dh^2. Traces with T < 0, or t = 0, add nothing; E = 0 gives
+    S = 0 and a zero gradient.
     """
     x = np.asarray(x, np.float64)
     dm = np.asarray(dm, np.float64)
     h = np.asarray(h, np.float64)
-    D = 1 if op == CMP else 3
+    D = {CMP: 1, CRS: 3, FOCRS: 5}[op]
     T = traveltime_sq(op, theta, t0, dm, h)
     a = window_amplitudes(x, T, dt, w)
     N = a.shape[0]
@@ -119,6 +135,9 @@ def semblance_grad(x, dt, dm, h, t0, op, theta, w):
     dS_du = np.where(ok, np.sum(dS_da * slope, axis=1), 0.0)
     if op == CMP:
         dT = [h * h]
+    elif op == FOCRS:
+        q = t0 + float(theta[0]) * dm + float(theta[1]) * h
+        dT = [2.0 * q * dm, 2.0 * q * h, dm * dm, dm * h, h * h]
     else:
         A = float(theta[0])
         dT = [2.0 * (t0 + A * dm) * dm, dm * dm, h * h]
@@ -137,6 +156,8 @@ def _domain_geometry(traces, mid, off, prob, d):
     x = np.asarray(traces[idx], np.float64)
     dm = np.asarray(mid[idx], np.float64) - float(prob.group_m0[g])
     h = np.asarray(off[idx], np.float64)
+    if prob.op == FOCRS:   # offset displacement from the section's central offset
+        h = h - float(prob.group_h0[g])
     t0 = float(prob.dom_it0[d]) * dt
     return x, dt, dm, h, t0
 
@@ -145,7 +166,7 @@ def semblance_many(traces, mid, off, prob, theta, domains=None):
     """S[d, p] for theta [n_dom, P, D] (or [len(domains), P, D]).
 
     ``prob`` is any object with the attributes op, half_window, group_m0,
-    group_dt, ap_ptr, ap_idx, dom_it0, dom_group.
+    group_dt, ap_ptr, ap_idx, dom_it0, dom_group (and group_h0 for FO-CRS).
     """
     theta = np.asarray(theta)
     doms = range(theta.shape[0]) if domains is None else domains
@@ -172,5 +193,6 @@ def semblance_grad_many(traces, mid, off, prob, theta, domains=None):
 
 
 def domain_data(traces, mid, off, prob, d):
-    """Aperture traces and geometry of domain d: (x, dt, dm, h, t0)."""
+    """Aperture traces and geometry of domain d: (x, dt, dm, h, t0); for
+    FO-CRS h is the offset displacement dh = h - h0."""
     return _domain_geometry(traces, mid, off, prob, d)

@@ -12,7 +12,8 @@ import dataclasses
 
 import numpy as np
 
-from .gathers import CMP, CRS, Line, Problem, make_line, cmp_problem, line_problem, batched_problems
+from .gathers import (CMP, CRS, FOCRS, Line, Problem, make_line, cmp_problem, line_problem,
+                      fo_problem, batched_problems)
 
 
 @dataclasses.dataclass
@@ -53,6 +54,12 @@ C_BOUNDS_CMP = (1.0 / 4500.0 ** 2, 1.0 / 1400.0 ** 2)
 CRS_LO = (-6e-4, -1.5e-7, 1.0 / 4800.0 ** 2)
 CRS_HI = (6e-4, 1.5e-7, 1.0 / 1400.0 ** 2)
 POLISH_LR = 2e-4
+# FO-CRS (Am, Ah, Bmm, Bmh, Bhh) on a common-offset section at h0 <= 2350 m,
+# from the recentring formulas over the crs_line generating ranges near the
+# events (|Am| <~ |A|, 0 <= Ah = C h0 / t0 <= sqrt(C) <= 1/1400,
+# Bmm = A^2 + B - Am^2, Bmh = -2 Am Ah, 0 <= Bhh = C - Ah^2 <= C), widened
+FO_LO = (-6e-4, -1e-4, -3e-7, -1e-6, -2e-8)
+FO_HI = (6e-4, 8e-4, 3e-7, 1e-6, 1.0 / 1400.0 ** 2 + 2e-8)
 
 
 def cmp_search(seed: int = 0, *, ns: int = 500, n_events: int = 8, np_: int = 32,
@@ -89,6 +96,28 @@ def crs_line(seed: int = 0, *, n_cmp: int = 200, ns: int = 1500, n_events: int =
                   exch_every=exch_every, polish_steps=polish_steps, polish_lr=POLISH_LR)
     return Workload(f"crs_line_{n_cmp}x48x{ns}", line.traces, line.mid, line.off, dt, prob, de,
                     line=line)
+
+
+def fo_panel(seed: int = 0, *, n_cmp: int = 200, ns: int = 1500, n_events: int = 20,
+             h0: float = 1000.0, ap_half: int = 8, off_half: float = 1000.0, np_: int = 64,
+             ng: int = 100, exch_every: int = 10, polish_steps: int = 0, cmps=None,
+             t0_range=None, snr: float = 3.0, tau_max: float | None = None) -> Workload:
+    """FO-CRS (Am, Ah, Bmm, Bmh, Bhh) search on the common-offset section at
+    h0 = 1000 m of the CRS line's data (200 CMPs x 48 offsets x 1500 samples
+    at 4 ms, 20 events, SNR 3): midpoint aperture +-8 CMPs (+-100 m), offset
+    aperture +-1000 m (41 offsets), window 11, DE 64 x 100 with exchange."""
+    dt = 0.004
+    tmax = (ns - 1) * dt
+    line = make_line(n_cmp=n_cmp, dcmp=12.5, offsets=OFF_48, ns=ns, dt=dt, n_events=n_events,
+                     tau_range=(0.2, tau_max if tau_max else 0.93 * tmax),
+                     A_range=(-4e-4, 4e-4), B_range=(-1e-7, 1e-7), v_range=(1500.0, 4500.0),
+                     snr=snr, seed=seed)
+    prob = fo_problem(line, half_window=5, h0=h0, ap_half=ap_half, off_half=off_half,
+                      cmps=cmps, t0_range=t0_range)
+    de = DEConfig(np=np_, ng=ng, F=0.5, CR=0.9, seed=seed, lo=FO_LO, hi=FO_HI,
+                  exch_every=exch_every, polish_steps=polish_steps, polish_lr=POLISH_LR)
+    return Workload(f"fo_{n_cmp}x48x{ns}_h{int(h0)}", line.traces, line.mid, line.off, dt, prob,
+                    de, line=line)
 
 
 def batched(seed: int = 0, *, n_prob: int = 4096, ntr_range=(16, 240), ns_range=(750, 3000),

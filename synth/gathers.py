@@ -30,6 +30,7 @@ import numpy as np
 
 CMP = 0  # operator id: CMP hyperbola, theta = (C,)
 CRS = 1  # operator id: zero-offset CRS surface, theta = (A, B, C)
+FOCRS = 2  # operator id: finite-offset CRS, theta = (Am, Ah, Bmm, Bmh, Bhh)
 
 
 @dataclasses.dataclass
@@ -62,6 +63,7 @@ class Problem:
     dom_group: np.ndarray   # int32 [n_dom]
     n_m0: int = 0           # exchange grid: domains laid out m0-major,
     n_t0: int = 0           # d = im0 * n_t0 + it0 (0 if no grid)
+    group_h0: np.ndarray | None = None  # float32 [G] central offset (FO-CRS only)
 
     @property
     def n_dom(self) -> int:
@@ -73,7 +75,7 @@ class Problem:
 
     @property
     def dim(self) -> int:
-        return 1 if self.op == CMP else 3
+        return {CMP: 1, CRS: 3, FOCRS: 5}[self.op]
 
     def aperture(self, g: int) -> np.ndarray:
         return self.ap_idx[self.ap_ptr[g]:self.ap_ptr[g + 1]]
@@ -142,6 +144,33 @@ def cmp_problem(line: Line, *, half_window: int, cmp_index: int = 0,
                    ap_ptr=np.array([0, idx.size], np.int32), ap_idx=idx,
                    dom_it0=it0, dom_group=np.zeros(it0.size, np.int32),
                    n_m0=1, n_t0=int(it0.size))
+
+
+def fo_problem(line: Line, *, half_window: int, h0: float, ap_half: int, off_half: float,
+               cmps=None, t0_range=None) -> Problem:
+    """FO-CRS problem on the common-offset section at full offset h0: one
+    group per CMP, aperture = traces of the CMPs within +-ap_half with
+    |h - h0| <= off_half; domains (m0, it0) laid out m0-major, it0 indexing
+    the section's time t(m0, h0)."""
+    cmps = np.arange(line.n_cmp) if cmps is None else np.asarray(cmps)
+    t0s = np.arange(line.ns) if t0_range is None else np.arange(*t0_range)
+    offs = line.off[:line.n_off].astype(np.float64)
+    sel = np.nonzero(np.abs(offs - h0) <= off_half + 1e-9)[0]
+    ptr = [0]
+    idx = []
+    for c in cmps:
+        c0, c1 = max(0, c - ap_half), min(line.n_cmp - 1, c + ap_half)
+        rows = (np.arange(c0, c1 + 1)[:, None] * line.n_off + sel[None, :]).ravel()
+        idx.append(rows.astype(np.int32))
+        ptr.append(ptr[-1] + rows.size)
+    G = len(cmps)
+    return Problem(op=FOCRS, half_window=half_window,
+                   group_m0=line.cmp_x[cmps].astype(np.float32),
+                   group_dt=np.full(G, line.dt, np.float32),
+                   ap_ptr=np.array(ptr, np.int32), ap_idx=np.concatenate(idx),
+                   dom_it0=np.tile(t0s.astype(np.int32), G),
+                   dom_group=np.repeat(np.arange(G, dtype=np.int32), t0s.size),
+                   n_m0=G, n_t0=int(t0s.size), group_h0=np.full(G, h0, np.float32))
 
 
 def line_problem(line: Line, *, half_window: int, ap_half: int, cmps=None,
@@ -228,6 +257,29 @@ def batched_problems(*, n_prob: int, ntr_range, ns_range, dts, seed: int,
                    dom_it0=np.concatenate(it0s), dom_group=np.concatenate(groups))
     info = dict(ntr=ntr, ns=nsp, dt=dtp, events=events, ns_max=ns_max)
     return traces, mid, off, prob, info
+
+
+def fo_recentre(event, m0: float, h0: float):
+    """Exact FO-CRS parameters of an event surface re-expanded about the
+    central point (m0, h0) of a common-offset section.
+
+    With Dc = m0 - m_e, t^2 = (tau + A Dc + A dm)^2 + B (Dc + dm)^2 +
+    C (h0 + dh)^2 is the quadratic c00 + c10 dm + c01 dh + c20 dm^2 +
+    c02 dh^2 (no dm dh term) with c00 = (tau + A Dc)^2 + B Dc^2 + C h0^2,
+    c10 = 2 A (tau + A Dc) + 2 B Dc, c01 = 2 C h0, c20 = A^2 + B, c02 = C.
+    Matching (t0 + Am dm + Ah dh)^2 + Bmm dm^2 + Bmh dm dh + Bhh dh^2 term by
+    term: t0 = sqrt(c00), Am = c10 / (2 t0), Ah = c01 / (2 t0),
+    Bmm = c20 - Am^2, Bmh = -2 Am Ah, Bhh = c02 - Ah^2. Returns
+    (t0, Am, Ah, Bmm, Bmh, Bhh) or None where c00 <= 0."""
+    m_e, tau, A, B, C = (float(v) for v in event[:5])
+    dc = m0 - m_e
+    c00 = (tau + A * dc) ** 2 + B * dc * dc + C * h0 * h0
+    if c00 <= 0.0:
+        return None
+    t0 = math.sqrt(c00)
+    Am = (A * (tau + A * dc) + B * dc) / t0
+    Ah = C * h0 / t0
+    return t0, Am, Ah, A * A + B - Am * Am, -2.0 * Am * Ah, C - Ah * Ah
 
 
 def crs_recentre(event, m0: float):

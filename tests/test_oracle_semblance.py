@@ -13,7 +13,7 @@ import pytest
 
 from oracle import semblance as osm
 
-CMP, CRS = osm.CMP, osm.CRS
+CMP, CRS, FOCRS = osm.CMP, osm.CRS, osm.FOCRS
 
 
 def load_worked(path):
@@ -24,11 +24,11 @@ def load_worked(path):
             continue
         key, *vals = line.split()
         if key == "case":
-            cur = dict(name=vals[0], traces=[])
+            cur = dict(name=vals[0], traces=[], h0=0.0)
             cases.append(cur)
         elif key == "op":
-            cur["op"] = CMP if vals[0] == "CMP" else CRS
-        elif key in ("dt", "m0", "expect", "stack"):
+            cur["op"] = {"CMP": CMP, "CRS": CRS, "FOCRS": FOCRS}[vals[0]]
+        elif key in ("dt", "m0", "h0", "expect", "stack"):
             cur[key] = float(vals[0])
         elif key in ("w", "it0"):
             cur[key] = int(vals[0])
@@ -49,6 +49,8 @@ def test_hand_worked_cases(golden_dir):
         x = np.zeros((len(m), ns))
         for i, t in enumerate(c["traces"]):
             x[i, :len(t) - 2] = t[2:]
+        if c["op"] == FOCRS:
+            h = h - c["h0"]
         S = osm.semblance(x, c["dt"], m - c["m0"], h, c["it0"] * c["dt"], c["op"], c["theta"],
                           c["w"])
         assert S == pytest.approx(c["expect"], abs=1e-14), c["name"]

@@ -32,6 +32,8 @@ def test_hand_worked_stacks(golden_dir):
         x = np.zeros((len(m), ns))
         for i, t in enumerate(c["traces"]):
             x[i, :len(t) - 2] = t[2:]
+        if c["op"] == osm.FOCRS:
+            h = h - c["h0"]
         v = ost.stack(x, c["dt"], m - c["m0"], h, c["it0"] * c["dt"], c["op"], c["theta"])
         assert v == pytest.approx(c["stack"], abs=1e-14), c["name"]
 
