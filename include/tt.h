@@ -51,12 +51,17 @@ enum {
 };
 
 /* Traveltime operators (readings of the operators the paper cites, Sec. 1):
- *   TT_OP_CMP:  T = t0^2 + C h^2                          theta = (C)
- *   TT_OP_CRS:  T = (t0 + A dm)^2 + B dm^2 + C h^2        theta = (A, B, C)
+ *   TT_OP_CMP:   T = t0^2 + C h^2                         theta = (C)
+ *   TT_OP_CRS:   T = (t0 + A dm)^2 + B dm^2 + C h^2       theta = (A, B, C)
+ *   TT_OP_FOCRS: T = (t0 + Am dm + Ah dh)^2 + Bmm dm^2 + Bmh dm dh + Bhh dh^2
+ *                theta = (Am, Ah, Bmm, Bmh, Bhh): the hyperbolic finite-offset
+ *                CRS operator (two slopes, three curvatures) for the sample
+ *                t0 of the common-offset section at central offset h0,
+ *                dh = h - h0 (tt_problem.group_h0)
  * with dm = m - m0 the midpoint displacement and h the full offset of a
  * trace (metres), t = sqrt(T) (seconds); a trace with T < 0 contributes
  * zero amplitudes and still counts in N. */
-enum { TT_OP_CMP = 0, TT_OP_CRS = 1 };
+enum { TT_OP_CMP = 0, TT_OP_CRS = 1, TT_OP_FOCRS = 2 };
 
 /* Storage type of the context's copy of the traces (arithmetic is FP32). */
 enum { TT_STORE_F32 = 0, TT_STORE_BF16 = 1 };
@@ -79,7 +84,7 @@ typedef struct tt_gathers {
 /* Domains and apertures. Domains sharing a midpoint, sample interval and
  * aperture form a group; apertures are CSR lists of trace indices. */
 typedef struct tt_problem {
-  int32_t op;            /* TT_OP_CMP or TT_OP_CRS                           */
+  int32_t op;            /* TT_OP_CMP, TT_OP_CRS or TT_OP_FOCRS             */
   int32_t half_window;   /* w: the window is the 2w+1 samples t + k dt,      */
                          /* k = -w..w (Sec. 2, W_l = 2w+1), 0 <= w <= 8      */
   int32_t n_groups;
@@ -93,6 +98,8 @@ typedef struct tt_problem {
   int32_t n_m0, n_t0;    /* exchange grid: if n_m0 * n_t0 == n_dom the       */
                          /* domains are laid out m0-major, d = im0*n_t0+it;  */
                          /* 0, 0 = no grid (no exchange)                     */
+  const float* group_h0; /* [n_groups] central full offset h0 (m) of each    */
+                         /* group: TT_OP_FOCRS only (NULL otherwise)         */
 } tt_problem;
 
 /* Search settings (Sec. 2.1: NP, NG, p = 1; F and CR fixed, or adapted as
@@ -341,8 +348,8 @@ tt_status tt_search(tt_ctx* ctx, float* best_theta, float* best_S, uint64_t* n_e
  * table and a validation flag) is a fixed device array of
  * TT_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
  * the library until the process exits; problems whose aperture lists hold
- * more than TT_NOALLOC_MAX_APERTURE_ENTRIES entries are rejected with
- * TT_ERR_UNSUPPORTED. The first call on a device (with that device current)
+ * more than TT_NOALLOC_MAX_APERTURE_ENTRIES entries, and TT_OP_FOCRS problems,
+ * are rejected with TT_ERR_UNSUPPORTED. The first call on a device (with that device current)
  * looks up the array's device address; make it before any stream capture.
  * Every call synchronises `stream` once, to read ap_ptr and the result of the
  * on-device validation (INVALID_ARG as for tt_ctx_create), then enqueues the

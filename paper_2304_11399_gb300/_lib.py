@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(PKG, "libtt.so")
 
 TT_OK, TT_ERR_INVALID_ARG, TT_ERR_CUDA, TT_ERR_OUT_OF_MEMORY, TT_ERR_TIMEOUT, \
     TT_ERR_UNSUPPORTED = range(6)
-TT_OP_CMP, TT_OP_CRS = 0, 1
+TT_OP_CMP, TT_OP_CRS, TT_OP_FOCRS = 0, 1, 2
 TT_OPT_KERNEL, TT_OPT_BLOCK, TT_OPT_SEARCH_GRAPH, TT_OPT_SPLIT = 1, 2, 3, 4
 TT_SPLIT_MAX_PAIRS = 152 * 8 * 64
 TT_KERNEL_PACKED, TT_KERNEL_PERSISTENT, TT_KERNEL_SCALAR = 1, 2, 3
@@ -37,7 +37,8 @@ class Gathers(C.Structure):
 class ProblemT(C.Structure):
     _fields_ = [("op", I32), ("half_window", I32), ("n_groups", I32), ("n_dom", I32),
                 ("group_m0", P), ("group_dt", P), ("ap_ptr", P), ("ap_idx", P),
-                ("dom_it0", P), ("dom_group", P), ("n_m0", I32), ("n_t0", I32)]
+                ("dom_it0", P), ("dom_group", P), ("n_m0", I32), ("n_t0", I32),
+                ("group_h0", P)]
 
 
 class DECfg(C.Structure):

@@ -225,15 +225,15 @@ enum : int {
 __device__ void flag(int* err, int code) { atomicCAS(err, 0, code); }
 
 __global__ void k_validate(int n_traces, int G, int n_dom, const float* g_dt, const float* g_m0,
-                           const int* ap_ptr, const int* ap_idx, long long nnz,
-                           const int* dom_it0, const int* dom_group, int* err) {
+                           const float* g_h0, const int* ap_ptr, const int* ap_idx,
+                           long long nnz, const int* dom_it0, const int* dom_group, int* err) {
   long long stride = (long long)gridDim.x * blockDim.x;
   long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (long long i = i0; i < G; i += stride) {
     if (ap_ptr[i] > ap_ptr[i + 1]) flag(err, kErrApPtr);
     float dt = g_dt[i];
     if (!(dt > 0.f) || !isfinite(dt)) flag(err, kErrDt);
-    if (!isfinite(g_m0[i])) flag(err, kErrGeom);
+    if (!isfinite(g_m0[i]) || (g_h0 && !isfinite(g_h0[i]))) flag(err, kErrGeom);
   }
   for (long long i = i0; i < nnz; i += stride) {
     int r = ap_idx[i];
@@ -270,9 +270,11 @@ __global__ void k_pad_rows(const float* __restrict__ src, T* __restrict__ dst, l
   }
 }
 
-// One warp per group: aperture entry e of group g -> (dm, dm^2, h^2, row base).
+// One warp per group: aperture entry e of group g -> (dm, dm^2, h^2, row base),
+// or for FO-CRS (g_h0 != NULL) -> (dm, dh = h - h0, 0, row base).
 __global__ void k_ap_table(int G, const int* ap_ptr, const int* ap_idx, const float* g_m0,
-                           const float* mid, const float* off, int pitch, float4* tab) {
+                           const float* g_h0, const float* mid, const float* off, int pitch,
+                           float4* tab) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= G) return;
@@ -282,7 +284,10 @@ __global__ void k_ap_table(int G, const int* ap_ptr, const int* ap_idx, const fl
     float dm = mid[r] - m0;
     float h = off[r];
     unsigned base = unsigned(r) * unsigned(pitch) + unsigned(tt::kPadFront);
-    tab[e] = make_float4(dm, dm * dm, h * h, __uint_as_float(base));
+    if (g_h0)
+      tab[e] = make_float4(dm, h - g_h0[warp], 0.f, __uint_as_float(base));
+    else
+      tab[e] = make_float4(dm, dm * dm, h * h, __uint_as_float(base));
   }
 }
 
@@ -364,8 +369,10 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
     return tt_fail(nullptr, TT_ERR_INVALID_ARG, "negative size");
   if (ga->storage != TT_STORE_F32 && ga->storage != TT_STORE_BF16)
     return tt_fail(nullptr, TT_ERR_INVALID_ARG, "storage must be TT_STORE_F32 or TT_STORE_BF16");
-  if (pr->op != TT_OP_CMP && pr->op != TT_OP_CRS)
-    return tt_fail(nullptr, TT_ERR_INVALID_ARG, "op must be TT_OP_CMP or TT_OP_CRS");
+  if (pr->op != TT_OP_CMP && pr->op != TT_OP_CRS && pr->op != TT_OP_FOCRS)
+    return tt_fail(nullptr, TT_ERR_INVALID_ARG, "op must be TT_OP_CMP, TT_OP_CRS or TT_OP_FOCRS");
+  if (pr->op == TT_OP_FOCRS && pr->n_groups > 0 && !pr->group_h0)
+    return tt_fail(nullptr, TT_ERR_INVALID_ARG, "FO-CRS needs group_h0");
   if (pr->half_window < 0 || pr->half_window > TT_MAX_HALF_WINDOW)
     return tt_fail(nullptr, TT_ERR_UNSUPPORTED, "half_window %d outside 0..%d", pr->half_window,
                    TT_MAX_HALF_WINDOW);
@@ -380,7 +387,7 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
   long long pitch = tt::padded_pitch(ga->ns);
   if ((long long)ga->n_traces * pitch >= (1ll << 32))
     return tt_fail(nullptr, TT_ERR_UNSUPPORTED, "padded trace buffer exceeds 2^32 samples");
-  const int D = pr->op == TT_OP_CMP ? 1 : 3;
+  const int D = tt::op_dim(pr->op);
   if (cfg) {
     if (cfg->np < 4 || cfg->np > 1024)
       return tt_fail(nullptr, TT_ERR_INVALID_ARG, "np %d outside 4..1024", cfg->np);
@@ -446,8 +453,9 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
     k_validate<<<grid_for(std::max<long long>({(long long)pr->n_groups, c->nnz,
                                                (long long)pr->n_dom})),
                  256, 0, s>>>(ga->n_traces, pr->n_groups, pr->n_dom, pr->group_dt,
-                              pr->group_m0, pr->ap_ptr, pr->ap_idx, c->nnz, pr->dom_it0,
-                              pr->dom_group, c->d_err);
+                              pr->group_m0, pr->op == TT_OP_FOCRS ? pr->group_h0 : nullptr,
+                              pr->ap_ptr, pr->ap_idx, c->nnz, pr->dom_it0, pr->dom_group,
+                              c->d_err);
     TRY(cudaGetLastError(), "validate");
   }
   if (ga->n_traces > 0 && ga->ns > 0) {
@@ -502,7 +510,8 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
     k_inv<<<(c->n_groups + 255) / 256, 256, 0, s>>>(c->n_groups, pr->group_dt, c->g_inv_dt);
     TRY(cudaGetLastError(), "inv dt");
     k_ap_table<<<(c->n_groups * 32 + 255) / 256, 256, 0, s>>>(
-        c->n_groups, pr->ap_ptr, pr->ap_idx, pr->group_m0, ga->mid, ga->off, c->pitch, c->ap_tab);
+        c->n_groups, pr->ap_ptr, pr->ap_idx, pr->group_m0,
+        pr->op == TT_OP_FOCRS ? pr->group_h0 : nullptr, ga->mid, ga->off, c->pitch, c->ap_tab);
     TRY(cudaGetLastError(), "aperture table");
   }
   if (c->n_dom > 0) {

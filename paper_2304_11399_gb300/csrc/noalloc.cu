@@ -184,6 +184,9 @@ extern "C" tt_status tt_semblance_eval_noalloc(const tt_gathers* ga, const tt_pr
     return tt_fail(nullptr, TT_ERR_INVALID_ARG,
                    "the allocation-free path reads float32 traces in place (storage must be "
                    "TT_STORE_F32)");
+  if (pr->op == TT_OP_FOCRS)
+    return tt_fail(nullptr, TT_ERR_UNSUPPORTED,
+                   "the allocation-free path evaluates TT_OP_CMP and TT_OP_CRS only");
   if (pr->op != TT_OP_CMP && pr->op != TT_OP_CRS)
     return tt_fail(nullptr, TT_ERR_INVALID_ARG, "op must be TT_OP_CMP or TT_OP_CRS");
   if (pr->half_window < 0 || pr->half_window > TT_MAX_HALF_WINDOW)

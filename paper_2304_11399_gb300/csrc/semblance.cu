@@ -1,611 +1,34 @@
-// Semblance of a traveltime operator (K1) and its adjoint gradient (K2).
-//
-// Work decomposition: (domain, individual) pairs are laid out domain-major;
-// a warp owns 64 consecutive pairs, so with NP = 64 it covers one domain,
-// and consecutive warps cover adjacent t0 at the same m0. Consecutive
-// domains share a group (same m0, same aperture), so every lane of a warp
-// walks the same aperture entries in the same order: the geometry-table load
-// is a warp-uniform broadcast and the 2w+2 samples each lane reads from a
-// trace row sit at nearby addresses for nearby t0 and for a converging
-// population, which the L1 cache turns into reuse.
-//
-// Per aperture trace i (Sec. 2, the W_l x T_a inner loop of eq. order), in
-// sample units (A' = A/dt, B' = B/dt^2, C' = C/dt^2, p0 = it0), the position
-// u = t/dt of the window centre is found, then
-//   j = floor(u), f = u - j, g = 1 - f,
-//   a_k = g x[j+k] + f x[j+k+1],  s_k += a_k,  E += a_k^2
-// and S = sum_k s_k^2 / (N E) (0 when E = 0).
-//
-// Two ways to find u, chosen by the record length at launch:
-//  * direct (records up to 2048 samples, u <= 2048 + w):
-//      q = p0 + A' dm,  U = q^2 + B' dm^2 + C' h^2,  u = sqrt(U)
-//    whose FP32 rounding stays within ~1e-4 samples there;
-//  * moveout (longer records): u = p0 + du with du the root of
-//      du^2 + 2 p0 du - V = 0,  V = x (x + 2 p0) + B' dm^2 + C' h^2,  x = A' dm,
-//    taken as du0 = U r - p0 (r ~ U^-1/2 from the hardware, one rounding)
-//    refined by one Newton step du = du0 - (du0 (du0 + 2 p0) - V) r / 2.
-//    p0 is an exact integer and du is tens of samples for deep events, so
-//    the fraction keeps ~1e-5-sample accuracy where u itself (thousands of
-//    samples) would round at ~1e-4 samples.
-// U < 0 (no real traveltime) gives NaN, which the clamp maps to ns + w: a
-// window of padding zeros. The scalar and the packed code run the same
-// operations; no product is ever rounded and then added (a pattern a compiler
-// may fuse), so they agree bit for bit.
-#include "tt_internal.cuh"
+// Launch logic and entry points of the semblance kernels (semblance_kernels.cuh):
+// forward evaluation (K1 in its packed, persistent, scalar and small-launch
+// split forms), the adjoint gradient (K2) and the stacked output.
+#include "semblance_kernels.cuh"
 
 namespace tt {
+namespace sk {
+extern template KFn pick_kernel<TT_OP_CMP>(int, int, int, bool);
+extern template KFn pick_kernel<TT_OP_CRS>(int, int, int, bool);
+extern template KFn pick_kernel<TT_OP_FOCRS>(int, int, int, bool);
+extern template SFn pick_stack<TT_OP_CMP>(int, bool);
+extern template SFn pick_stack<TT_OP_CRS>(int, bool);
+extern template SFn pick_stack<TT_OP_FOCRS>(int, bool);
+}  // namespace sk
+
 namespace {
 
-__device__ __forceinline__ float sqrt_approx(float x) {
-  float y;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ float rsqrt_approx(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-template <typename T>
-__device__ __forceinline__ float ld_sample(const T* p);
-template <>
-__device__ __forceinline__ float ld_sample<float>(const float* p) {
-  return __ldg(p);
-}
-template <>
-__device__ __forceinline__ float ld_sample<__nv_bfloat16>(const __nv_bfloat16* p) {
-  unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(p));
-  return __uint_as_float(unsigned(u) << 16);
-}
-
-// Per-lane constants of one (domain, individual) pair.
-struct Lane {
-  int d, e0, e1, p0i;
-  float p0, ca, cb, cc, inv_dt;
-  float two_p0, p0sq;  // 2 p0, p0^2 + 1e-30 (the bias keeps U = 0 finite under rsqrt)
-  float lim, neg_p0;   // moveout: du is clamped to [-p0, ns + w - p0]
-  float umax;          // direct: u is clamped to ns + w
-};
-
-// L.d is the local domain (indexing theta and S); its geometry comes from the
-// global domain dom_map[L.d] when a map is given (a subset evaluation).
-template <int OP>
-__device__ __forceinline__ bool lane_setup(const EvalArgs& a, long long q, Lane& L) {
-  if (q >= (long long)a.n_dom * a.P) return false;
-  L.d = int(q / a.P);
-  const int gd = a.dom_map ? a.dom_map[L.d] : L.d;
-  if (gd < 0) return false;
-  const int g = a.dom_group[gd];
-  L.inv_dt = a.g_inv_dt[g];
-  L.e0 = a.ap_ptr[g];
-  L.e1 = a.ap_ptr[g + 1];
-  L.p0i = a.dom_it0[gd];
-  L.p0 = float(L.p0i);
-  const float* th = a.theta + q * (OP == TT_OP_CMP ? 1 : 3);
-  const float i2 = L.inv_dt * L.inv_dt;
-  if (OP == TT_OP_CMP) {
-    L.ca = 0.f;
-    L.cb = 0.f;
-    L.cc = th[0] * i2;
-  } else {
-    L.ca = th[0] * L.inv_dt;
-    L.cb = th[1] * i2;
-    L.cc = th[2] * i2;
-  }
-  L.two_p0 = 2.f * L.p0;
-  L.p0sq = __fmul_rn(L.p0, L.p0) + 1e-30f;
-  L.lim = a.umax - L.p0;
-  L.neg_p0 = -L.p0;
-  L.umax = a.umax;
-  return true;
-}
-
-// Position of one pair on one trace. Every operation is rounded once, in the
-// same order as one lane of the packed path, so both give identical bits.
-struct Pos {
-  int j;       // window sample k sits at j - W + k
-  float f, g;  // interpolation weights
-  float u;     // clamped position (samples)
-  float q;     // p0 + A' dm (for the gradient)
-};
-
-template <int OP, bool MOVEOUT>
-__device__ __forceinline__ Pos locate(const Lane& L, float4 t4) {
-  Pos P;
-  if (!MOVEOUT) {
-    float U;
-    if (OP == TT_OP_CMP) {
-      P.q = L.p0;
-      U = fmaf(L.cc, t4.z, __fmul_rn(L.p0, L.p0));
-    } else {
-      P.q = fmaf(L.ca, t4.x, L.p0);
-      U = fmaf(L.cb, t4.y, fmaf(L.cc, t4.z, __fmul_rn(P.q, P.q)));
-    }
-    P.u = fminf(sqrt_approx(U), L.umax);
-    const float fl = truncf(P.u);
-    P.f = __fsub_rn(P.u, fl);
-    P.g = __fsub_rn(1.f, P.f);
-    P.j = int(fl);
-    return P;
-  }
-  float V, x;
-  if (OP == TT_OP_CMP) {
-    x = 0.f;
-    V = __fmul_rn(L.cc, t4.z);
-  } else {
-    x = __fmul_rn(L.ca, t4.x);
-    const float w = fmaf(L.cb, t4.y, __fmul_rn(L.cc, t4.z));
-    V = fmaf(x, __fadd_rn(x, L.two_p0), w);
-  }
-  const float U = __fadd_rn(L.p0sq, V);
-  const float r = rsqrt_approx(U);
-  const float du0 = fmaf(U, r, L.neg_p0);
-  const float res = fmaf(du0, __fadd_rn(du0, L.two_p0), __fmul_rn(V, -1.f));
-  float du = fmaf(res, __fmul_rn(r, -0.5f), du0);
-  du = fmaxf(fminf(du, L.lim), L.neg_p0);
-  const float fl = floorf(du);
-  P.f = fmaf(fl, -1.f, du);
-  P.g = fmaf(P.f, -1.f, 1.f);
-  P.j = L.p0i + int(fl);
-  P.u = L.p0 + du;
-  P.q = L.p0 + x;
-  return P;
-}
-
-// Final normalisation S = Q / (N E). FP32-stored traces: E is one FP32
-// sum over the aperture. BF16-stored traces (long apertures, reduced-
-// precision data): E is accumulated in FP32 within chunks of 32 aperture
-// traces and the chunk sums are added in FP64, so the energy's rounding
-// error stays that of a 32-trace FP32 sum; the division is done in FP64.
-template <typename T>
-struct Chunk {
-  static constexpr bool kF64 = false;
-  static constexpr int kTraces = 1 << 30;  // one chunk: the whole aperture
-};
-template <>
-struct Chunk<__nv_bfloat16> {
-  static constexpr bool kF64 = true;
-  static constexpr int kTraces = 32;
-};
-
-template <typename T>
-__device__ __forceinline__ float normalise(float Q, int N, float E, double Ed) {
-  if (Chunk<T>::kF64) return (Ed > 0.0) ? float(double(Q) / (double(N) * Ed)) : 0.f;
-  return (E > 0.f) ? Q / (float(N) * E) : 0.f;
-}
-
-__device__ __forceinline__ void store_S(const EvalArgs& a, long long q, int d, float S) {
-  if (a.slots) {
-    const int slot = a.slots[q];
-    if (slot >= 0) a.S[(size_t)d * a.np_out + slot] = S;
-  } else {
-    a.S[q] = S;
-  }
-}
-
-// Accumulate one pair over aperture entries [r0, r1): the stack sums s_k and
-// the energy -- one FP32 sum over the range (FP32 storage), or the FP64 sum
-// of FP32 sums over 32-entry chunks from r0 (BF16 storage).
-template <int OP, int W, typename T, bool MV>
-__device__ __forceinline__ void acc_scalar(const EvalArgs& a, const Lane& L, int r0, int r1,
-                                           float* s, float& E, double& Ed) {
-  constexpr int K = 2 * W + 1;
-  const T* __restrict__ tr = static_cast<const T*>(a.traces);
-  for (int c0 = r0, c1; c0 < r1; c0 = c1) {
-    c1 = (r1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : r1;
-    float Ec = 0.f;
-    for (int e = c0; e < c1; ++e) {
-      const float4 t4 = __ldg(a.ap_tab + e);
-      const Pos P = locate<OP, MV>(L, t4);
-      const T* x = tr + (__float_as_uint(t4.w) + P.j - W);
-      float xv[K + 1];
-#pragma unroll
-      for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float ak = fmaf(P.f, xv[k + 1], __fmul_rn(P.g, xv[k]));
-        s[k] = __fadd_rn(s[k], ak);
-        Ec = fmaf(ak, ak, Ec);
-      }
-    }
-    if (Chunk<T>::kF64) Ed += double(Ec); else E = Ec;
-  }
-}
-
-// The same for two pairs sharing an aperture, with packed FP32x2 arithmetic:
-// sample k of the two pairs forms one register pair, so every interpolation,
-// stack and energy update is one f32x2 instruction for both (same operations
-// and bits as two acc_scalar calls).
-template <int OP, int W, typename T, bool MV>
-__device__ __forceinline__ void acc_packed(const EvalArgs& a, const Lane& L0, const Lane& L1,
-                                           int r0, int r1, float2* s, float2& E, double& Ed0,
-                                           double& Ed1) {
-  constexpr int K = 2 * W + 1;
-  const T* __restrict__ tr = static_cast<const T*>(a.traces);
-  const float2 ca = make_float2(L0.ca, L1.ca), cb = make_float2(L0.cb, L1.cb),
-               cc = make_float2(L0.cc, L1.cc), two_p0 = make_float2(L0.two_p0, L1.two_p0),
-               p0sq = make_float2(L0.p0sq, L1.p0sq), neg_p0 = make_float2(L0.neg_p0, L1.neg_p0),
-               p0v = make_float2(L0.p0, L1.p0);
-  const float2 p0p0 = __fmul2_rn(p0v, p0v);
-  const float2 m1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f),
-               mhalf = make_float2(-0.5f, -0.5f);
-  for (int c0 = r0, c1; c0 < r1; c0 = c1) {
-    c1 = (r1 - c0 > Chunk<T>::kTraces) ? c0 + Chunk<T>::kTraces : r1;
-    float2 Ec = make_float2(0.f, 0.f);
-    for (int e = c0; e < c1; ++e) {
-      const float4 t4 = __ldg(a.ap_tab + e);
-      float2 f, g;
-      int j0, j1;
-      if constexpr (!MV) {
-        float2 U;
-        if (OP == TT_OP_CMP) {
-          U = __ffma2_rn(cc, make_float2(t4.z, t4.z), p0p0);
-        } else {
-          const float2 qv = __ffma2_rn(ca, make_float2(t4.x, t4.x), p0v);
-          U = __ffma2_rn(cc, make_float2(t4.z, t4.z), __fmul2_rn(qv, qv));
-          U = __ffma2_rn(cb, make_float2(t4.y, t4.y), U);
-        }
-        const float u0 = fminf(sqrt_approx(U.x), L0.umax), u1 = fminf(sqrt_approx(U.y), L1.umax);
-        const float fl0 = truncf(u0), fl1 = truncf(u1);
-        f = make_float2(__fsub_rn(u0, fl0), __fsub_rn(u1, fl1));
-        g = make_float2(__fsub_rn(1.f, f.x), __fsub_rn(1.f, f.y));
-        j0 = int(fl0);
-        j1 = int(fl1);
-      } else {
-        float2 V;
-        if (OP == TT_OP_CMP) {
-          V = __fmul2_rn(cc, make_float2(t4.z, t4.z));
-        } else {
-          const float2 x = __fmul2_rn(ca, make_float2(t4.x, t4.x));
-          const float2 w = __ffma2_rn(cb, make_float2(t4.y, t4.y),
-                                      __fmul2_rn(cc, make_float2(t4.z, t4.z)));
-          V = __ffma2_rn(x, __fadd2_rn(x, two_p0), w);
-        }
-        const float2 U = __fadd2_rn(p0sq, V);
-        const float2 r = make_float2(rsqrt_approx(U.x), rsqrt_approx(U.y));
-        const float2 du0 = __ffma2_rn(U, r, neg_p0);
-        const float2 res = __ffma2_rn(du0, __fadd2_rn(du0, two_p0), __fmul2_rn(V, m1));
-        float2 du = __ffma2_rn(res, __fmul2_rn(r, mhalf), du0);
-        du.x = fmaxf(fminf(du.x, L0.lim), L0.neg_p0);
-        du.y = fmaxf(fminf(du.y, L1.lim), L1.neg_p0);
-        const float2 fl = make_float2(floorf(du.x), floorf(du.y));
-        f = __ffma2_rn(fl, m1, du);
-        g = __ffma2_rn(f, m1, one);
-        j0 = L0.p0i + int(fl.x);
-        j1 = L1.p0i + int(fl.y);
-      }
-      const unsigned base = __float_as_uint(t4.w) - W;
-      const T* x0 = tr + (base + j0);
-      const T* x1 = tr + (base + j1);
-      float2 xv[K + 1];
-#pragma unroll
-      for (int k = 0; k <= K; ++k) xv[k] = make_float2(ld_sample<T>(x0 + k), ld_sample<T>(x1 + k));
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float2 ak = __ffma2_rn(f, xv[k + 1], __fmul2_rn(g, xv[k]));
-        s[k] = __fadd2_rn(s[k], ak);
-        Ec = __ffma2_rn(ak, ak, Ec);
-      }
-    }
-    if (Chunk<T>::kF64) {
-      Ed0 += double(Ec.x);
-      Ed1 += double(Ec.y);
-    } else {
-      E = Ec;
-    }
-  }
-}
-
-// Scalar evaluation of one (domain, individual) pair over its aperture.
-template <int OP, int W, typename T, bool MV>
-__device__ __forceinline__ float eval_scalar(const EvalArgs& a, const Lane& L) {
-  constexpr int K = 2 * W + 1;
-  float s[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) s[k] = 0.f;
-  float E = 0.f;
-  double Ed = 0.0;
-  acc_scalar<OP, W, T, MV>(a, L, L.e0, L.e1, s, E, Ed);
-  float Q = 0.f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
-  return normalise<T>(Q, L.e1 - L.e0, E, Ed);
-}
-
-__device__ __forceinline__ bool same_aperture(const Lane& L0, const Lane& L1) {
-  return L1.e0 == L0.e0 && L1.e1 == L0.e1 && L1.inv_dt == L0.inv_dt;
-}
-
-// One 64-pair unit: each thread evaluates pairs q and q + 32 (either may be
-// absent: past the end, or a domain the map skips). When both lie in one
-// group (the common case: same aperture, possibly different t0) the
-// aperture is walked once with packed arithmetic; otherwise each pair is
-// evaluated on its own (same operations, same bits).
-template <int OP, int W, typename T, bool MV>
-__device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int lane) {
-  constexpr int K = 2 * W + 1;
-  const long long q0 = unit * 64 + lane, q1 = q0 + 32;
-  Lane L0, L1;
-  const bool v0 = lane_setup<OP>(a, q0, L0);
-  const bool v1 = lane_setup<OP>(a, q1, L1);
-  if (!v0 || !v1 || !same_aperture(L0, L1)) {
-    if (v0) store_S(a, q0, L0.d, eval_scalar<OP, W, T, MV>(a, L0));
-    if (v1) store_S(a, q1, L1.d, eval_scalar<OP, W, T, MV>(a, L1));
-    return;
-  }
-  float2 s[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) s[k] = make_float2(0.f, 0.f);
-  float2 E = make_float2(0.f, 0.f);
-  double Ed0 = 0.0, Ed1 = 0.0;
-  acc_packed<OP, W, T, MV>(a, L0, L1, L0.e0, L0.e1, s, E, Ed0, Ed1);
-  float2 Q = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int k = 0; k < K; ++k) Q = __ffma2_rn(s[k], s[k], Q);
-  const int N = L0.e1 - L0.e0;
-  store_S(a, q0, L0.d, normalise<T>(Q.x, N, E.x, Ed0));
-  store_S(a, q1, L1.d, normalise<T>(Q.y, N, E.y, Ed1));
-}
-
-// K1 for small launches (few 64-pair units): a block of kSplitWarps warps
-// shares one unit, warp w walking the w-th contiguous slice of every pair's
-// aperture; the slices' partial sums meet in shared memory and are added in
-// slice order. Its summation order (per slice, then across slices) differs
-// from the one-warp-per-unit kernel, so it is chosen by launch size alone --
-// every variant of a small launch runs it -- and results stay reproducible.
-constexpr int kSplitWarps = 8;
-static_assert(TT_SPLIT_MAX_PAIRS % 64 == 0, "split threshold is counted in 64-pair units");
-constexpr long long kSplitMaxUnits = TT_SPLIT_MAX_PAIRS / 64;
-
-template <int OP, int W, typename T, bool MV>
-__global__ void __launch_bounds__(32 * kSplitWarps) k_semblance_split(const EvalArgs a) {
-  constexpr int K = 2 * W + 1;
-  __shared__ float part_s[kSplitWarps][64][K];
-  __shared__ float part_E[kSplitWarps][64];
-  __shared__ double part_Ed[kSplitWarps][64];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long unit = blockIdx.x;
-  const long long q0 = unit * 64 + lane, q1 = q0 + 32;
-  Lane L0, L1;
-  const bool v0 = lane_setup<OP>(a, q0, L0);
-  const bool v1 = lane_setup<OP>(a, q1, L1);
-  auto slice = [&](const Lane& L, int& r0, int& r1) {
-    const long long n = L.e1 - L.e0;
-    r0 = L.e0 + int(n * w / kSplitWarps);
-    r1 = L.e0 + int(n * (w + 1) / kSplitWarps);
-  };
-  if (v0 && v1 && same_aperture(L0, L1)) {
-    int r0, r1;
-    slice(L0, r0, r1);
-    float2 s[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) s[k] = make_float2(0.f, 0.f);
-    float2 E = make_float2(0.f, 0.f);
-    double Ed0 = 0.0, Ed1 = 0.0;
-    acc_packed<OP, W, T, MV>(a, L0, L1, r0, r1, s, E, Ed0, Ed1);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      part_s[w][lane][k] = s[k].x;
-      part_s[w][lane + 32][k] = s[k].y;
-    }
-    part_E[w][lane] = E.x;
-    part_E[w][lane + 32] = E.y;
-    part_Ed[w][lane] = Ed0;
-    part_Ed[w][lane + 32] = Ed1;
-  } else {
-    for (int h = 0; h < 2; ++h) {
-      const Lane& L = h ? L1 : L0;
-      if (!(h ? v1 : v0)) continue;
-      int r0, r1;
-      slice(L, r0, r1);
-      float s[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) s[k] = 0.f;
-      float E = 0.f;
-      double Ed = 0.0;
-      acc_scalar<OP, W, T, MV>(a, L, r0, r1, s, E, Ed);
-      const int p = lane + 32 * h;
-#pragma unroll
-      for (int k = 0; k < K; ++k) part_s[w][p][k] = s[k];
-      part_E[w][p] = E;
-      part_Ed[w][p] = Ed;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 64) {
-    const int p = threadIdx.x;
-    Lane L;
-    if (!lane_setup<OP>(a, unit * 64 + p, L)) return;
-    float Q = 0.f, E = 0.f;
-    double Ed = 0.0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      float sk = 0.f;
-      for (int v = 0; v < kSplitWarps; ++v) sk = __fadd_rn(sk, part_s[v][p][k]);
-      Q = fmaf(sk, sk, Q);
-    }
-    for (int v = 0; v < kSplitWarps; ++v) {
-      E = __fadd_rn(E, part_E[v][p]);
-      Ed += part_Ed[v][p];
-    }
-    store_S(a, unit * 64 + p, L.d, normalise<T>(Q, L.e1 - L.e0, E, Ed));
-  }
-}
-
-// K1, grid-mapped (queue == nullptr: one 64-pair unit per warp, the grid
-// covers every unit) or persistent (a grid sized to the GPU; after its first
-// unit a warp takes the next one from an atomic counter, so warps whose
-// apertures are short take more units).
-template <int OP, int W, typename T, bool MV>
-__global__ void __launch_bounds__(kBlock) k_semblance(const EvalArgs a) {
-  const int lane = threadIdx.x & 31;
-  const long long n_units = ((long long)a.n_dom * a.P + 63) / 64;
-  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  long long unit = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  while (unit < n_units) {
-    eval_unit<OP, W, T, MV>(a, unit, lane);
-    if (!a.queue) break;
-    __syncwarp();
-    unsigned long long next = 0;
-    if (lane == 0) next = atomicAdd(a.queue, 1ull);
-    unit = warps + (long long)__shfl_sync(0xffffffffu, next, 0);
-  }
-}
-
-// K1, one (domain, individual) pair per thread.
-template <int OP, int W, typename T, bool MV>
-__global__ void __launch_bounds__(kBlock) k_semblance_scalar(const EvalArgs a) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  Lane L;
-  if (!lane_setup<OP>(a, q, L)) return;
-  store_S(a, q, L.d, eval_scalar<OP, W, T, MV>(a, L));
-}
-
-// K2: two passes over the aperture. Pass 1 = K1 (s_k, E, S). With
-// alpha = 2/(N E), beta = 2 S / E, dS/da_ik = alpha s_k - beta a_ik, so pass 2
-// forms dS/du_i = sum_k (alpha s_k - beta a_ik)(x[j+k+1] - x[j+k]) and
-// chains it through du/dtheta (u = p0 + du in samples, q = p0 + A' dm):
-//   du/dA = q dm / (u dt),  du/dB = dm^2 / (2 u dt^2),  du/dC = h^2 / (2 u dt^2).
-// Positions clamped to the all-zero window and u = 0 contribute nothing.
-template <int OP, int W, typename T, bool MV>
-__global__ void __launch_bounds__(kBlock) k_semblance_grad(const EvalArgs a) {
-  constexpr int K = 2 * W + 1;
-  constexpr int D = OP == TT_OP_CMP ? 1 : 3;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  Lane L;
-  if (!lane_setup<OP>(a, q, L)) return;
-  const T* __restrict__ tr = static_cast<const T*>(a.traces);
-  float s[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) s[k] = 0.f;
-  float E = 0.f;
-  for (int e = L.e0; e < L.e1; ++e) {
-    const float4 t4 = __ldg(a.ap_tab + e);
-    const Pos P = locate<OP, MV>(L, t4);
-    const T* x = tr + (__float_as_uint(t4.w) + P.j - W);
-    float xv[K + 1];
-#pragma unroll
-    for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float ak = fmaf(P.f, xv[k + 1], __fmul_rn(P.g, xv[k]));
-      s[k] += ak;
-      E = fmaf(ak, ak, E);
-    }
-  }
-  float Q = 0.f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
-  const float N = float(L.e1 - L.e0);
-  const float S = (E > 0.f) ? Q / (N * E) : 0.f;
-  float G0 = 0.f, G1 = 0.f, G2 = 0.f;
-  if (E > 0.f) {
-    const float alpha = 2.f / (N * E);
-    const float beta = 2.f * S / E;
-    for (int e = L.e0; e < L.e1; ++e) {
-      const float4 t4 = __ldg(a.ap_tab + e);
-      const Pos P = locate<OP, MV>(L, t4);
-      const T* x = tr + (__float_as_uint(t4.w) + P.j - W);
-      float xv[K + 1];
-#pragma unroll
-      for (int k = 0; k <= K; ++k) xv[k] = ld_sample<T>(x + k);
-      float sg = 0.f, ag = 0.f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float gk = xv[k + 1] - xv[k];
-        const float ak = fmaf(P.f, xv[k + 1], __fmul_rn(P.g, xv[k]));
-        sg = fmaf(s[k], gk, sg);
-        ag = fmaf(ak, gk, ag);
-      }
-      const float dSdu = fmaf(alpha, sg, -beta * ag);
-      const float inv_u = (P.u > 0.f && P.u < L.umax) ? 1.f / P.u : 0.f;
-      const float c = dSdu * inv_u;
-      if (OP == TT_OP_CRS) {
-        G0 = fmaf(c * P.q, t4.x, G0);
-        G1 = fmaf(0.5f * c, t4.y, G1);
-      }
-      G2 = fmaf(0.5f * c, t4.z, G2);
-    }
-  }
-  a.S[q] = S;
-  float* out = a.dS + q * D;
-  const float i2 = L.inv_dt * L.inv_dt;
-  if (OP == TT_OP_CRS) {
-    out[0] = G0 * L.inv_dt;
-    out[1] = G1 * i2;
-    out[2] = G2 * i2;
-  } else {
-    out[0] = G2 * i2;
-  }
-}
-
-using KFn = void (*)(const EvalArgs);
-
-// Stacked output: one warp per domain (P = 1, theta [n_dom][D]); lane l sums
-// the centre amplitudes of aperture entries e0 + l, e0 + l + 32, ... in order,
-// the 32 lane sums meet in a butterfly, and the mean is one FP32 division.
-// Positions are those of the semblance window's centre sample (same clamp:
-// T < 0 or past the record reads the zero padding).
-template <int OP, typename T, bool MV>
-__global__ void __launch_bounds__(256) k_stack(const EvalArgs a, float* __restrict__ out) {
-  const long long d = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  Lane L;
-  if (!lane_setup<OP>(a, d, L)) return;  // warp-uniform: the whole warp leaves
-  const T* __restrict__ tr = static_cast<const T*>(a.traces);
-  float s = 0.f;
-  for (int e = L.e0 + lane; e < L.e1; e += 32) {
-    const float4 t4 = __ldg(a.ap_tab + e);
-    const Pos P = locate<OP, MV>(L, t4);
-    const T* x = tr + (__float_as_uint(t4.w) + P.j);
-    s = __fadd_rn(s, fmaf(P.f, ld_sample<T>(x + 1), __fmul_rn(P.g, ld_sample<T>(x))));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
-  if (lane == 0) {
-    const int N = L.e1 - L.e0;
-    out[L.d] = N > 0 ? __fdiv_rn(s, float(N)) : 0.f;
-  }
-}
+using sk::KFn;
+using sk::kSplitMaxUnits;
+using sk::kSplitWarps;
 
 constexpr int kDirectMax = 2048;  // direct position up to u = 2048 samples
 
-#define TT_W_TABLE(NAME)                                                                  \
-  template <int OP, typename T, bool MV>                                                  \
-  KFn NAME##_pick(int W) {                                                                \
-    switch (W) {                                                                          \
-      case 0: return NAME<OP, 0, T, MV>;                                                  \
-      case 1: return NAME<OP, 1, T, MV>;                                                  \
-      case 2: return NAME<OP, 2, T, MV>;                                                  \
-      case 3: return NAME<OP, 3, T, MV>;                                                  \
-      case 4: return NAME<OP, 4, T, MV>;                                                  \
-      case 5: return NAME<OP, 5, T, MV>;                                                  \
-      case 6: return NAME<OP, 6, T, MV>;                                                  \
-      case 7: return NAME<OP, 7, T, MV>;                                                  \
-      case 8: return NAME<OP, 8, T, MV>;                                                  \
-    }                                                                                     \
-    return nullptr;                                                                       \
-  }                                                                                       \
-  template <bool MV>                                                                      \
-  KFn NAME##_select2(int op, int storage, int W) {                                        \
-    const bool bf = storage == TT_STORE_BF16;                                             \
-    if (op == TT_OP_CMP)                                                                  \
-      return bf ? NAME##_pick<TT_OP_CMP, __nv_bfloat16, MV>(W)                            \
-                : NAME##_pick<TT_OP_CMP, float, MV>(W);                                   \
-    return bf ? NAME##_pick<TT_OP_CRS, __nv_bfloat16, MV>(W)                              \
-              : NAME##_pick<TT_OP_CRS, float, MV>(W);                                     \
-  }                                                                                       \
-  KFn NAME##_select(int op, int storage, int W, bool mv) {                                \
-    return mv ? NAME##_select2<true>(op, storage, W) : NAME##_select2<false>(op, storage, W); \
+KFn pick(int kind, const EvalArgs& a, bool mv) {
+  switch (a.op) {
+    case TT_OP_CMP: return sk::pick_kernel<TT_OP_CMP>(kind, a.storage, a.W, mv);
+    case TT_OP_CRS: return sk::pick_kernel<TT_OP_CRS>(kind, a.storage, a.W, mv);
+    case TT_OP_FOCRS: return sk::pick_kernel<TT_OP_FOCRS>(kind, a.storage, a.W, mv);
   }
-
-TT_W_TABLE(k_semblance)
-TT_W_TABLE(k_semblance_scalar)
-TT_W_TABLE(k_semblance_split)
-TT_W_TABLE(k_semblance_grad)
-#undef TT_W_TABLE
+  return nullptr;
+}
 
 cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
   const long long n = (long long)a.n_dom * a.P;
@@ -617,19 +40,19 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
   long long blocks;
   EvalArgs b = a;
   if (grad) {
-    fn = k_semblance_grad_select(a.op, a.storage, a.W, mv);
+    fn = pick(sk::kKindGrad, a, mv);
     blocks = (n + block - 1) / block;
   } else if (a.split && (n + 63) / 64 < kSplitMaxUnits) {
     // few units: a block per unit, the aperture split over its warps
-    fn = k_semblance_split_select(a.op, a.storage, a.W, mv);
+    fn = pick(sk::kKindSplit, a, mv);
     if (!fn) return cudaErrorInvalidValue;
     fn<<<unsigned((n + 63) / 64), 32 * kSplitWarps, 0, s>>>(b);
     return cudaGetLastError();
   } else if (a.kernel == TT_KERNEL_SCALAR) {
-    fn = k_semblance_scalar_select(a.op, a.storage, a.W, mv);
+    fn = pick(sk::kKindScalar, a, mv);
     blocks = (n + block - 1) / block;
   } else {
-    fn = k_semblance_select(a.op, a.storage, a.W, mv);
+    fn = pick(sk::kKindPacked, a, mv);
     const long long units = (n + 63) / 64;
     blocks = (units + block / 32 - 1) / (block / 32);
     if (a.kernel == TT_KERNEL_PERSISTENT && a.queue) {
@@ -660,20 +83,19 @@ cudaError_t launch_stack(const EvalArgs& a, float* out, cudaStream_t s) {
   if (a.n_dom == 0) return cudaSuccess;
   if (a.P != 1) return cudaErrorInvalidValue;
   const bool mv = a.umax > float(kDirectMax);
-  using SFn = void (*)(const EvalArgs, float*);
-  SFn fn = nullptr;
-  const bool bf = a.storage == TT_STORE_BF16;
-  if (a.op == TT_OP_CMP)
-    fn = bf ? (mv ? k_stack<TT_OP_CMP, __nv_bfloat16, true> : k_stack<TT_OP_CMP, __nv_bfloat16, false>)
-            : (mv ? k_stack<TT_OP_CMP, float, true> : k_stack<TT_OP_CMP, float, false>);
-  else
-    fn = bf ? (mv ? k_stack<TT_OP_CRS, __nv_bfloat16, true> : k_stack<TT_OP_CRS, __nv_bfloat16, false>)
-            : (mv ? k_stack<TT_OP_CRS, float, true> : k_stack<TT_OP_CRS, float, false>);
+  sk::SFn fn = nullptr;
+  switch (a.op) {
+    case TT_OP_CMP: fn = sk::pick_stack<TT_OP_CMP>(a.storage, mv); break;
+    case TT_OP_CRS: fn = sk::pick_stack<TT_OP_CRS>(a.storage, mv); break;
+    case TT_OP_FOCRS: fn = sk::pick_stack<TT_OP_FOCRS>(a.storage, mv); break;
+  }
+  if (!fn) return cudaErrorInvalidValue;
   const long long blocks = ((long long)a.n_dom * 32 + 255) / 256;
   if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
   fn<<<unsigned(blocks), 256, 0, s>>>(a, out);
   return cudaGetLastError();
 }
+
 cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s) { return launch(a, s, true); }
 
 }  // namespace tt

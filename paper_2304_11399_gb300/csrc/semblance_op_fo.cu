@@ -1,0 +1,9 @@
+// Instantiations of the semblance kernels for the FO-CRS operator.
+#include "semblance_kernels.cuh"
+
+namespace tt {
+namespace sk {
+template KFn pick_kernel<TT_OP_FOCRS>(int, int, int, bool);
+template SFn pick_stack<TT_OP_FOCRS>(int, bool);
+}  // namespace sk
+}  // namespace tt

@@ -12,6 +12,9 @@
 
 namespace tt {
 
+// parameters per operator: CMP (C), CRS (A, B, C), FO-CRS (Am, Ah, Bmm, Bmh, Bhh)
+constexpr int op_dim(int op) { return op == TT_OP_CMP ? 1 : op == TT_OP_CRS ? 3 : 5; }
+
 // Padded trace layout: sample n of trace r lives at r * pitch + kPadFront + n.
 // kPadFront >= max half window; kPadBack >= 2 * max half window + 2 so that a
 // window whose position is clamped to ns + w reads only padding zeros.

@@ -103,12 +103,16 @@ def tt_ctx_create(traces, mid, off, problem, cfg=None, *, storage: str = "f32",
                 ap_idx=_dev(problem.ap_idx, torch.int32, device),
                 dom_it0=_dev(problem.dom_it0, torch.int32, device),
                 dom_group=_dev(problem.dom_group, torch.int32, device))
+    h0 = getattr(problem, "group_h0", None)
+    if h0 is not None:
+        arrs["group_h0"] = _dev(h0, torch.float32, device)
     n_groups = int(arrs["group_m0"].numel())
     n_dom = int(arrs["dom_it0"].numel())
     p = L.ProblemT(int(problem.op), int(problem.half_window), n_groups, n_dom,
                    *(arrs[k].data_ptr() for k in ("group_m0", "group_dt", "ap_ptr", "ap_idx",
                                                  "dom_it0", "dom_group")),
-                   int(getattr(problem, "n_m0", 0)), int(getattr(problem, "n_t0", 0)))
+                   int(getattr(problem, "n_m0", 0)), int(getattr(problem, "n_t0", 0)),
+                   arrs["group_h0"].data_ptr() if h0 is not None else None)
     cfg_p = None
     npop = 0
     if cfg is not None:
@@ -127,7 +131,7 @@ def tt_ctx_create(traces, mid, off, problem, cfg=None, *, storage: str = "f32",
     with torch.cuda.device(device):
         st = lib.tt_ctx_create(C.byref(h), C.byref(g), C.byref(p), cfg_p, _stream(stream))
     _check(lib, None, st)
-    D = 1 if int(problem.op) == L.TT_OP_CMP else 3
+    D = {L.TT_OP_CMP: 1, L.TT_OP_CRS: 3, L.TT_OP_FOCRS: 5}[int(problem.op)]
     return Context(h, n_dom, D, npop, int(getattr(problem, "n_m0", 0)),
                    int(getattr(problem, "n_t0", 0)), device, lib)
 

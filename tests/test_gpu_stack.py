@@ -52,7 +52,8 @@ def test_hand_worked_stacks_through_cabi(golden_dir):
                              ap_ptr=np.array([0, len(m)], np.int32),
                              ap_idx=np.arange(len(m), dtype=np.int32),
                              dom_it0=np.array([c["it0"]], np.int32),
-                             dom_group=np.array([0], np.int32))
+                             dom_group=np.array([0], np.int32),
+                             group_h0=np.array([c["h0"]], np.float32))
         out = _stack(x, m, h, prob, np.array([c["theta"]], np.float32))
         assert abs(out[0] - c["stack"]) <= 1e-6, c["name"]
 

@@ -52,13 +52,36 @@ def test_version_and_error_without_gpu(lib):
     assert not h.value
 
 
-def test_binding_struct_layout_matches_header():
-    # natural C alignment of the three structs, as laid out in tt.h
-    assert ctypes.sizeof(_lib.Gathers) == 40
-    assert ctypes.sizeof(_lib.ProblemT) == 72
-    assert _lib.DECfg.seed.offset == 16
-    assert _lib.DECfg.exch_every.offset == 88
-    assert ctypes.sizeof(_lib.DECfg) == 104
+def test_binding_struct_layout_matches_header(tmp_path):
+    """The ctypes structs against the C compiler's layout of include/tt.h:
+    size and every field offset."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"tt_gathers": _lib.Gathers, "tt_problem": _lib.ProblemT,
+               "tt_de_cfg": _lib.DECfg, "tt_ens_cfg": _lib.EnsCfg, "tt_stats": _lib.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tt.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, *_ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            *key, val = ln.split()
+            got[tuple(key)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, *_ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
 
 
 def test_package_has_no_cpu_fallback():

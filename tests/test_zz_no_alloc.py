@@ -95,6 +95,12 @@ def test_noalloc_rejects_oversize_and_invalid_input():
     S = torch.zeros((1, 1), device=dev())
     assert _noalloc(lib, g, p, th, S) == _lib.TT_ERR_UNSUPPORTED
     assert b"at most" in lib.tt_last_error(None)
+    # the FO-CRS operator is evaluated through a context only
+    fo = synth.Problem(**{**prob.__dict__})
+    fo.op = _lib.TT_OP_FOCRS
+    g, p, keep = _cabi_args(wl.traces, wl.mid, wl.off, fo)
+    assert _noalloc(lib, g, p, th, S) == _lib.TT_ERR_UNSUPPORTED
+    assert b"TT_OP_CRS only" in lib.tt_last_error(None)
     # an out-of-range trace index is caught on the device and reported
     bad = synth.Problem(**{**prob.__dict__})
     bad.ap_idx = prob.ap_idx.copy()
