@@ -34,7 +34,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ZO samples solved/s (CRS search with neighbour exchange + gradient polish)"
 UNIT = "ZO samples/s"
-FLOPS_PER_TRACE_EVAL = 75          # see the design doc, kernel K1
+# algorithmic FP32 flops per (trace, parameter vector) pair of K1 (an FMA
+# counts 2; the square root and its clamp 1 each): traveltime 9 (CRS; CMP 5,
+# FO-CRS 15), interpolation 33, stack 11, energy 22
+FLOPS_PER_TRACE_EVAL = {0: 71, 1: 75, 2: 81}  # by operator: CMP, CRS, FO-CRS
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -43,6 +46,9 @@ def workload_config(wl, n_gpus):
     if wl.info is not None:
         name = (f"{p.n_groups} uneven CRS problems, 16-240 traces and 750-3000 samples "
                 f"(dt 2/4 ms) each, every sample a domain, window 11")
+    elif p.op == 2:
+        name = ("FO-CRS on the common-offset section at h0 = 1000 m of the 200-CMP x 48 x "
+                "1500-sample line (dt 4 ms), aperture +-8 CMP x +-1000 m, window 11")
     else:
         sub = "" if p.n_m0 in (0, 200) else f" (first {p.n_m0} CMPs solved)"
         name = ("CRS line 200 CMP x 48 offsets x 1500 samples (dt 4 ms), aperture +-10 CMP, "
@@ -266,9 +272,10 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--cmps", type=int, default=0,
                     help="solve only the first CMPS midpoints of the line (profiling case)")
-    ap.add_argument("--workload", default="line", choices=["line", "batched"],
+    ap.add_argument("--workload", default="line", choices=["line", "batched", "fo"],
                     help="line: the 200-CMP CRS line (default); batched: 4096 uneven CRS "
-                         "problems (every sample a domain, DE 64 x 80, autotuned kernel)")
+                         "problems (every sample a domain, DE 64 x 80, autotuned kernel); fo: "
+                         "FO-CRS on the line's common-offset section at 1000 m")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -287,7 +294,8 @@ def main():
     import paper_2304_11399_gb300 as tt
     from synth import configs
 
-    wl = configs.crs_line(rank) if args.workload == "line" else configs.batched(rank)
+    wl = {"line": configs.crs_line, "batched": configs.batched,
+          "fo": configs.fo_panel}[args.workload](rank)
     wl.storage = args.storage
     if args.cmps and args.workload == "line":
         import synth
@@ -312,7 +320,7 @@ def main():
         tt.tt_de_step(ctx, 0, th)
         tuned = {f"{k}/{b}": round(v, 3) for (k, b), v in tt.tt_ctx_autotune(ctx, th).items()}
         del th
-    best_t = torch.empty((prob.n_dom, 3), dtype=torch.float32, device=dev)
+    best_t = torch.empty((prob.n_dom, ctx.D), dtype=torch.float32, device=dev)
     best_s = torch.empty((prob.n_dom,), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 18, dtype=torch.float32, device=dev)  # 256 MiB
 
@@ -370,7 +378,7 @@ def main():
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roof = None
     if stats["timed_launches"] > 0 and stats["semblance_ms"] > 0:
-        flops = stats["trace_evals"] * FLOPS_PER_TRACE_EVAL
+        flops = stats["trace_evals"] * FLOPS_PER_TRACE_EVAL[int(prob.op)]
         n_l = stats["semblance_launches"]
         achieved = (flops / n_l) / (stats["semblance_ms"] / stats["timed_launches"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

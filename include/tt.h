@@ -125,8 +125,8 @@ typedef struct tt_de_cfg {
                          /* parents of strictly better children (<= NP,     */
                          /* uniform replacement when full); mu moved by c   */
                          /* towards the mean CR and Lehmer-mean F of the    */
-                         /* successes. tt_search and tt_de_step only (the   */
-                         /* ENS sweep keeps F, CR fixed).                   */
+                         /* successes. tt_search, tt_de_step and the ENS    */
+                         /* sweep (a fresh memory and archive per sample).  */
 } tt_de_cfg;
 
 typedef struct tt_ctx tt_ctx;
@@ -206,6 +206,18 @@ tt_status tt_stack(tt_ctx* ctx, const float* theta, float* out, void* stream);
  * block); FP32 arithmetic with one rounding per operation, so results are
  * bit-reproducible. pop and fit [n_dom][NP] are updated in place;
  * best_idx [n_dom] may be NULL. */
+/* Copy the JADE adaptation state of a context created with cfg.adapt = 1
+ * out to (save = 1) or in from (save = 0) caller arrays, for checkpointing an
+ * adaptive search driven by tt_de_step: mu [n_dom][2] (mu_CR, mu_F), n_arc
+ * [n_dom] (archive fill), archive [n_dom][NP][D], F and CR [n_dom][NP] (the
+ * pending trial's F_i, CR_i). Device pointers owned by the caller; the paper
+ * has no counterpart (with Philox stateless, pop, fit, the pending trial and
+ * its fitness, the generation and this state are the whole search state).
+ * Asynchronous on `stream`. Errors: TT_ERR_INVALID_ARG without adaptation or
+ * for NULL arrays. */
+tt_status tt_jade_state(tt_ctx* ctx, int32_t save, float* mu, int32_t* n_arc, float* archive,
+                        float* F, float* CR, void* stream);
+
 tt_status tt_de_step(tt_ctx* ctx, int32_t gen, float* pop, float* fit, const float* trial,
                      const float* trial_fit, float* next_trial, int32_t* best_idx,
                      void* stream);

@@ -40,6 +40,9 @@ Readings taken where the paper is silent:
 * Interpolation weights in float32: w = (t - ta) / (tb - ta) correctly
   rounded, theta = theta_a + w (theta_b - theta_a), one rounding per
   operation.
+* With ``cfg.adapt`` the evolutions use JADE's adaptation (``oracle.jade``):
+  every estimated sample starts a fresh memory (mu_F, mu_CR = F, CR) and an
+  empty archive; the draws use the same counter generation codes.
 * Semblance calls are counted as the paper counts them (eq.
   ens_semblance): NP_f (1 + NG_f) per estimated sample in stage 0,
   NP_bf (1 + NG_bf) - 1 per estimated sample in a backward or forward stage
@@ -50,6 +53,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import de as de_mod
+from . import jade
 from .semblance import semblance_many
 
 f32 = np.float32
@@ -144,15 +148,26 @@ def ens_search(traces, mid, off, prob, cfg):
                         cfg.seed, d, i, lo, hi, gen=gen_code(s, 0))
             fit = semblance_many(traces, mid, off, prob, pop, domains=doms).astype(f32)
             n_calls += len(doms) * (NP if kind == "explore" else NP - 1)
+            adapt = bool(getattr(cfg, "adapt", 0))
+            states = [jade.new_state(NP, D, cfg.F, cfg.CR) for _ in doms] if adapt else None
             for g in range(1, NG + 1):
                 trial = np.empty_like(pop)
                 for r, d in enumerate(doms):
-                    trial[r], _ = de_mod.mutate_population(cfg.seed, d, gen_code(s, g), pop[r],
-                                                          fit[r], cfg.F, cfg.CR, lo, hi)
+                    if adapt:
+                        trial[r], _ = jade.trial_population(states[r], cfg.seed, d, gen_code(s, g),
+                                                            pop[r], fit[r], lo, hi)
+                    else:
+                        trial[r], _ = de_mod.mutate_population(cfg.seed, d, gen_code(s, g),
+                                                              pop[r], fit[r], cfg.F, cfg.CR, lo,
+                                                              hi)
                 tfit = semblance_many(traces, mid, off, prob, trial, domains=doms).astype(f32)
                 n_calls += len(doms) * NP
-                for r in range(len(doms)):
-                    pop[r], fit[r] = de_mod.select(pop[r], fit[r], trial[r], tfit[r])
+                for r, d in enumerate(doms):
+                    if adapt:
+                        pop[r], fit[r] = jade.select_adapt(states[r], cfg.seed, d, gen_code(s, g),
+                                                           pop[r], fit[r], trial[r], tfit[r])
+                    else:
+                        pop[r], fit[r] = de_mod.select(pop[r], fit[r], trial[r], tfit[r])
             for r, d in enumerate(doms):
                 b = de_mod.best_index(fit[r])
                 best_th[d], best_S[d] = pop[r, b], fit[r, b]

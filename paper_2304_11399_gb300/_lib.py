@@ -69,6 +69,7 @@ SIGNATURES = {
     "tt_semblance_eval": (I32, [P, P, I32, P, P]),
     "tt_semblance_grad": (I32, [P, P, I32, P, P, P]),
     "tt_stack": (I32, [P, P, P, P]),
+    "tt_jade_state": (I32, [P, I32, P, P, P, P, P, P]),
     "tt_de_step": (I32, [P, I32, P, P, P, P, P, P, P]),
     "tt_best_snapshot": (I32, [P, P, P, P, P, P]),
     "tt_neighbor_exchange": (I32, [P, I32, I32, P, P, P, P, P, P]),

@@ -475,6 +475,33 @@ extern "C" tt_status tt_de_step(tt_ctx* c, int32_t gen, float* pop, float* fit,
                        "de_step launch");
 }
 
+extern "C" tt_status tt_jade_state(tt_ctx* c, int32_t save, float* mu, int32_t* n_arc,
+                                   float* archive, float* F, float* CR, void* stream) {
+  tt_status st = need_cfg(c);
+  if (st != TT_OK) return st;
+  if (!c->cfg.adapt) return tt_fail(c, TT_ERR_INVALID_ARG, "context was created without adapt");
+  if (c->n_dom == 0) return TT_OK;
+  if (!mu || !n_arc || !archive || !F || !CR) return tt_fail(c, TT_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nd = size_t(c->n_dom), np = size_t(c->cfg.np), D = size_t(c->D);
+  struct {
+    void* ctx;
+    void* user;
+    size_t bytes;
+  } parts[] = {{c->jade_mu, mu, nd * 2 * 4},
+               {c->jade_na, n_arc, nd * 4},
+               {c->jade_arc, archive, nd * np * D * 4},
+               {c->jade_F, F, nd * np * 4},
+               {c->jade_CR, CR, nd * np * 4}};
+  for (auto& p : parts) {
+    cudaError_t e = save ? cudaMemcpyAsync(p.user, p.ctx, p.bytes, cudaMemcpyDeviceToDevice, s)
+                         : cudaMemcpyAsync(p.ctx, p.user, p.bytes, cudaMemcpyDeviceToDevice, s);
+    st = tt_cuda_check(c, e, "copy adaptation state");
+    if (st != TT_OK) return st;
+  }
+  return TT_OK;
+}
+
 extern "C" tt_status tt_best_snapshot(tt_ctx* c, const float* pop, const float* fit,
                                       float* best_theta, float* best_S, void* stream) {
   tt_status st = need_cfg(c);

@@ -75,13 +75,19 @@ __device__ __forceinline__ bool unset(const float* th) { return isnan(th[0]); }
 // trace in the exploration stage -- or a random member drawn from Philox.
 __global__ void k_ens_init(StepGeo g, int bf, int NP, int D, const int* map, const float* best_th,
                            float* pop, uint32_t key0, uint32_t key1, uint32_t gen,
-                           const float* lo, const float* hi) {
+                           const float* lo, const float* hi, float* jade_mu, int* jade_na,
+                           float F0, float CR0) {
   const long long n = (long long)g.n_buckets * g.n_est * NP;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const int r = int(q / NP), i = int(q - (long long)r * NP);
   const int d = map[r];
   if (d < 0) return;
+  if (jade_mu && i == 0) {  // a fresh JADE memory and an empty archive per sample
+    jade_mu[2 * (size_t)r] = CR0;
+    jade_mu[2 * (size_t)r + 1] = F0;
+    jade_na[r] = 0;
+  }
   const int t = d % g.n_t0, b = r / g.n_est;
   const bool has_prev = (g.tb - g.dirn) >= 0 && (g.tb - g.dirn) < bucket_len(g, b);
   const int dprev = d - g.dirn * g.n_t0;
@@ -219,7 +225,7 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
         const uint32_t gen0 = uint32_t(si + 1) * 65536u;
         k_ens_init<<<blocks((long long)n_est_loc * NP), 256, 0, s>>>(
             g, sg.bf ? 1 : 0, NP, D, map_est, bth, c->pop, key0, key1, gen0, c->bounds,
-            c->bounds + D);
+            c->bounds + D, c->cfg.adapt ? c->jade_mu : nullptr, c->jade_na, c->cfg.F, c->cfg.CR);
         STEP(c->counted(cudaGetLastError()), "ens init");
         tt::EvalArgs ea = c->eval_args(c->pop, NP, c->fit);
         ea.n_dom = n_est_loc;
@@ -230,7 +236,6 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
         bool pending = false;
         for (int gi = 1; gi <= NG; ++gi) {
           tt::DeArgs a = tt_make_de_args(c, int(gen0) + gi);
-          a.adapt = 0;  // the sweep's short evolutions keep F and CR fixed
           a.n_dom = n_est_loc;
           a.NP = NP;
           a.dom_map = map_est;
@@ -250,7 +255,7 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
         }
         if (pending) {
           tt::DeArgs a = tt_make_de_args(c, int(gen0) + NG + 1);
-          a.adapt = 0;
+          a.sel_gen = int(gen0) + NG;  // select-only: the last trial
           a.n_dom = n_est_loc;
           a.NP = NP;
           a.dom_map = map_est;

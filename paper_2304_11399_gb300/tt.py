@@ -201,6 +201,22 @@ def tt_de_step(ctx: Context, gen: int, pop, fit=None, trial=None, trial_fit=None
     return pop, fit, next_trial, best_idx
 
 
+def tt_jade_state(ctx: Context, state: dict | None = None, stream=None) -> dict:
+    """Save (state None: returns new tensors mu, n_arc, archive, F, CR) or
+    restore (state given) the context's JADE adaptation state."""
+    n, NP, D = ctx.n_dom, ctx.np, ctx.D
+    shapes = dict(mu=((n, 2), torch.float32), n_arc=((n,), torch.int32),
+                  archive=((n, NP, D), torch.float32), F=((n, NP), torch.float32),
+                  CR=((n, NP), torch.float32))
+    save = state is None
+    if save:
+        state = {k: torch.empty(s, dtype=dt, device=ctx.device) for k, (s, dt) in shapes.items()}
+    ptrs = [_ptr(state[k], k, dtype=dt, shape=s) for k, (s, dt) in shapes.items()]
+    _check(ctx.lib, ctx.handle,
+           ctx.lib.tt_jade_state(ctx.handle, 1 if save else 0, *ptrs, _stream(stream)))
+    return state
+
+
 def tt_best_snapshot(ctx: Context, pop, fit, stream=None):
     """(best_theta [n_dom, D], best_S [n_dom]) of a population."""
     bt = torch.empty((ctx.n_dom, ctx.D), dtype=torch.float32, device=pop.device)

@@ -36,6 +36,7 @@ class EnsCfg:
     seed: int = 11
     lo: tuple = configs.CRS_LO
     hi: tuple = configs.CRS_HI
+    adapt: int = 0
 
 
 def test_stage_lists_follow_the_paper():
@@ -76,14 +77,17 @@ def test_call_count_matches_eq_ens_semblance(n_skip, n_cycle, nb, n_m0):
         assert n * 3 == 34 * P_d  # the paper's 34/3 calls per sample at 5 x 1
 
 
-def test_ens_beats_jade_at_equal_cost_and_recovers():
-    """A small line with strong dipping events: ENS 5x1 vs JADE 5x1."""
+@pytest.mark.parametrize("adapt", [0, 1])
+def test_ens_beats_jade_at_equal_cost_and_recovers(adapt):
+    """A small line with strong dipping events: ENS 5x1 vs JADE 5x1, with
+    fixed F, CR or with JADE's adaptation in both (the paper's setting)."""
     wl = configs.crs_line(7, n_cmp=16, ns=150, n_events=3, ap_half=3, snr=8.0, tau_max=0.5)
     prob = synth.line_problem(wl.line, half_window=5, ap_half=3)
-    cfg = EnsCfg(n_bucket=16)
+    F, CR = (0.5, 0.5) if adapt else (0.5, 0.9)
+    cfg = EnsCfg(n_bucket=16, adapt=adapt, F=F, CR=CR)
     th_e, S_e, n_e = ens.ens_search(wl.traces, wl.mid, wl.off, prob, cfg)
-    jade = configs.DEConfig(np=5, ng=1, F=0.5, CR=0.9, seed=11, lo=configs.CRS_LO,
-                            hi=configs.CRS_HI)
+    jade = configs.DEConfig(np=5, ng=1, F=F, CR=CR, seed=11, lo=configs.CRS_LO,
+                            hi=configs.CRS_HI, adapt=adapt)
     th_j, S_j, n_j = osearch.search(wl.traces, wl.mid, wl.off, prob, jade)
     assert n_j == 10 * prob.n_dom
     assert abs(n_e - n_j) / n_j < 0.15         # 34/3 vs 10 calls per sample
