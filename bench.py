@@ -316,7 +316,7 @@ def main():
                            device=dev)
     tuned = None
     if args.workload == "batched":
-        th = torch.empty((prob.n_dom, wl.de.np, 3), dtype=torch.float32, device=dev)
+        th = torch.empty((prob.n_dom, wl.de.np, ctx.D), dtype=torch.float32, device=dev)
         tt.tt_de_step(ctx, 0, th)
         tuned = {f"{k}/{b}": round(v, 3) for (k, b), v in tt.tt_ctx_autotune(ctx, th).items()}
         del th
@@ -358,7 +358,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         host_tr = torch.from_numpy(wl.traces).pin_memory()
-        host_bt = torch.empty((prob.n_dom, 3), dtype=torch.float32).pin_memory()
+        host_bt = torch.empty((prob.n_dom, ctx.D), dtype=torch.float32).pin_memory()
         host_bs = torch.empty((prob.n_dom,), dtype=torch.float32).pin_memory()
         barrier()
         t0 = time.perf_counter()
