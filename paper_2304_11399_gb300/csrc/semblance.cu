@@ -17,7 +17,6 @@ namespace {
 
 using sk::KFn;
 using sk::kSplitMaxUnits;
-using sk::kSplitWarps;
 
 constexpr int kDirectMax = 2048;  // direct position up to u = 2048 samples
 
@@ -46,7 +45,13 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
     // few units: a block per unit, the aperture split over its warps
     fn = pick(sk::kKindSplit, a, mv);
     if (!fn) return cudaErrorInvalidValue;
-    fn<<<unsigned((n + 63) / 64), 32 * kSplitWarps, 0, s>>>(b);
+    const long long units = (n + 63) / 64;
+    const int S = sk::split_warps(units);
+    const size_t smem = sk::split_smem_bytes(S, a.W);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sk::split_smem_bytes(sk::kSplitMaxWarps, a.W)));
+    if (e != cudaSuccess) return e;
+    fn<<<unsigned(units), 32 * S, smem, s>>>(b);
     return cudaGetLastError();
   } else if (a.kernel == TT_KERNEL_SCALAR) {
     fn = pick(sk::kKindScalar, a, mv);

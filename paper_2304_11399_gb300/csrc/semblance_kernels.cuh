@@ -392,22 +392,41 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
   store_S(a, q1, L1.d, normalise<T>(Q.y, N, E.y, Ed1));
 }
 
-// K1 for small launches (few 64-pair units): a block of kSplitWarps warps
-// shares one unit, warp w walking the w-th contiguous slice of every pair's
-// aperture; the slices' partial sums meet in shared memory and are added in
-// slice order. Its summation order (per slice, then across slices) differs
-// from the one-warp-per-unit kernel, so it is chosen by launch size alone --
-// every variant of a small launch runs it -- and results stay reproducible.
-constexpr int kSplitWarps = 8;
+// K1 for small launches (few 64-pair units): a block of S warps shares one
+// unit, warp w walking the w-th contiguous slice of every pair's aperture;
+// the slices' partial sums meet in shared memory and are added in slice
+// order. S (8, 16 or 32, the block's warp count) grows as the launch shrinks
+// so that the GPU holds about 152 x 32 warps. The summation order (per
+// slice, then across slices) depends on S and differs from the
+// one-warp-per-unit kernel, so both are chosen by launch size alone -- every
+// variant of a launch runs the same kernel -- and results stay reproducible.
+constexpr int kSplitWarps = 8;       // S for the largest split launches
+constexpr int kSplitMaxWarps = 32;
 static_assert(TT_SPLIT_MAX_PAIRS % 64 == 0, "split threshold is counted in 64-pair units");
 constexpr long long kSplitMaxUnits = TT_SPLIT_MAX_PAIRS / 64;
 
+// warps per unit for a split launch of `units` 64-pair units
+inline int split_warps(long long units) {
+  const long long target = 152ll * 32;
+  if (units * 8 >= target) return 8;
+  if (units * 16 >= target) return 16;
+  return kSplitMaxWarps;
+}
+
+// dynamic shared memory of a split block: FP64 energies [S][64], FP32
+// energies [S][64], stack sums [S][64][K]
+inline size_t split_smem_bytes(int S, int W) {
+  return size_t(S) * 64 * (sizeof(double) + sizeof(float) + sizeof(float) * (2 * W + 1));
+}
+
 template <int OP, int W, typename T, bool MV>
-__global__ void __launch_bounds__(32 * kSplitWarps) k_semblance_split(const EvalArgs a) {
+__global__ void __launch_bounds__(32 * kSplitMaxWarps) k_semblance_split(const EvalArgs a) {
   constexpr int K = 2 * W + 1;
-  __shared__ float part_s[kSplitWarps][64][K];
-  __shared__ float part_E[kSplitWarps][64];
-  __shared__ double part_Ed[kSplitWarps][64];
+  extern __shared__ __align__(16) unsigned char split_smem[];
+  const int S = blockDim.x >> 5;
+  double* part_Ed = reinterpret_cast<double*>(split_smem);   // [S][64]
+  float* part_E = reinterpret_cast<float*>(part_Ed + S * 64);  // [S][64]
+  float* part_s = part_E + S * 64;                             // [S][64][K]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long unit = blockIdx.x;
   const long long q0 = unit * 64 + lane, q1 = q0 + 32;
@@ -416,8 +435,8 @@ __global__ void __launch_bounds__(32 * kSplitWarps) k_semblance_split(const Eval
   const bool v1 = lane_setup<OP>(a, q1, L1);
   auto slice = [&](const Lane& L, int& r0, int& r1) {
     const long long n = L.e1 - L.e0;
-    r0 = L.e0 + int(n * w / kSplitWarps);
-    r1 = L.e0 + int(n * (w + 1) / kSplitWarps);
+    r0 = L.e0 + int(n * w / S);
+    r1 = L.e0 + int(n * (w + 1) / S);
   };
   if (v0 && v1 && same_aperture(L0, L1)) {
     int r0, r1;
@@ -430,13 +449,13 @@ __global__ void __launch_bounds__(32 * kSplitWarps) k_semblance_split(const Eval
     acc_packed<OP, W, T, MV>(a, L0, L1, r0, r1, s, E, Ed0, Ed1);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      part_s[w][lane][k] = s[k].x;
-      part_s[w][lane + 32][k] = s[k].y;
+      part_s[(w * 64 + lane) * K + k] = s[k].x;
+      part_s[(w * 64 + lane + 32) * K + k] = s[k].y;
     }
-    part_E[w][lane] = E.x;
-    part_E[w][lane + 32] = E.y;
-    part_Ed[w][lane] = Ed0;
-    part_Ed[w][lane + 32] = Ed1;
+    part_E[w * 64 + lane] = E.x;
+    part_E[w * 64 + lane + 32] = E.y;
+    part_Ed[w * 64 + lane] = Ed0;
+    part_Ed[w * 64 + lane + 32] = Ed1;
   } else {
     for (int h = 0; h < 2; ++h) {
       const Lane& L = h ? L1 : L0;
@@ -451,9 +470,9 @@ __global__ void __launch_bounds__(32 * kSplitWarps) k_semblance_split(const Eval
       acc_scalar<OP, W, T, MV>(a, L, r0, r1, s, E, Ed);
       const int p = lane + 32 * h;
 #pragma unroll
-      for (int k = 0; k < K; ++k) part_s[w][p][k] = s[k];
-      part_E[w][p] = E;
-      part_Ed[w][p] = Ed;
+      for (int k = 0; k < K; ++k) part_s[(w * 64 + p) * K + k] = s[k];
+      part_E[w * 64 + p] = E;
+      part_Ed[w * 64 + p] = Ed;
     }
   }
   __syncthreads();
@@ -466,12 +485,12 @@ __global__ void __launch_bounds__(32 * kSplitWarps) k_semblance_split(const Eval
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       float sk = 0.f;
-      for (int v = 0; v < kSplitWarps; ++v) sk = __fadd_rn(sk, part_s[v][p][k]);
+      for (int v = 0; v < S; ++v) sk = __fadd_rn(sk, part_s[(v * 64 + p) * K + k]);
       Q = fmaf(sk, sk, Q);
     }
-    for (int v = 0; v < kSplitWarps; ++v) {
-      E = __fadd_rn(E, part_E[v][p]);
-      Ed += part_Ed[v][p];
+    for (int v = 0; v < S; ++v) {
+      E = __fadd_rn(E, part_E[v * 64 + p]);
+      Ed += part_Ed[v * 64 + p];
     }
     store_S(a, unit * 64 + p, L.d, normalise<T>(Q, L.e1 - L.e0, E, Ed));
   }

@@ -51,8 +51,10 @@ def batch():
     return configs.batched(3, n_prob=40, ng=80, domains_per_problem=48)
 
 
-@pytest.mark.parametrize("P", [1, 4, 64])
+@pytest.mark.parametrize("P", [1, 4, 20, 64])
 def test_variants_bit_identical_on_a_line(P):
+    """2400 domains: P = 1 and 4 split the aperture over 32 warps per unit,
+    P = 20 (750 units) over 8, P = 64 is too large to split."""
     wl = small_line(31)
     theta = random_theta(wl.problem.n_dom, P, wl.de.lo, wl.de.hi, P)
     ora = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, wl.problem, theta)
