@@ -318,7 +318,11 @@ tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
  *                 sums added in order; every variant then launches that kernel,
  *                 so S still does not depend on TT_OPT_KERNEL / TT_OPT_BLOCK,
  *                 but its rounding differs from the unsplit kernels' (both stay
- *                 within 1e-5 of the exact semblance). 0: never split.
+ *                 within 1e-5 of the exact semblance). The smallest launches
+ *                 also spread a unit over up to 4 blocks that combine their
+ *                 sums through the context's scratch, so split evaluations on
+ *                 one context must not overlap on the GPU (one stream, or
+ *                 events between streams). 0: never split.
  *  Changing an option drops a captured graph. */
 enum { TT_OPT_KERNEL = 1, TT_OPT_BLOCK = 2, TT_OPT_SEARCH_GRAPH = 3, TT_OPT_SPLIT = 4 };
 #define TT_SPLIT_MAX_PAIRS (152 * 8 * 64)

@@ -60,6 +60,10 @@ tt::EvalArgs tt_ctx::eval_args(const float* theta, int P, float* S) const {
   a.kernel = kernel;
   a.block = block;
   a.split = split ? 1 : 0;
+  a.split_blocks = 1;
+  a.split_part = split_part;
+  a.split_part_d = split_part_d;
+  a.split_ticket = split_ticket;
   a.queue = queue;
   return a;
 }
@@ -315,7 +319,8 @@ void free_ctx(tt_ctx* c) {
                   c->dom_it0, c->dom_group, c->bounds, c->pop, c->fit, c->trial[0],
                   c->trial[1], c->tfit[0], c->tfit[1], c->snap, c->imports, c->slots,
                   c->best_idx, c->pol_th, c->pol_g, c->pol_S, c->pol_bth, c->pol_bS, c->d_err,
-                  c->queue, c->out_th, c->out_S, c->jade_mu, c->jade_arc, c->jade_F,
+                  c->queue, c->split_part, c->split_part_d, c->split_ticket, c->out_th,
+                  c->out_S, c->jade_mu, c->jade_arc, c->jade_F,
                   c->jade_CR, c->jade_na};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -561,6 +566,12 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
     }
   }
   TRY(dalloc(&c->queue, 1), "alloc queue");
+  TRY(dalloc(&c->split_part, size_t(tt::kSplitPartSets) * 64 * tt::kSplitPartStride),
+      "alloc split scratch");
+  TRY(dalloc(&c->split_part_d, size_t(tt::kSplitPartSets) * 64), "alloc split scratch");
+  TRY(dalloc(&c->split_ticket, size_t(tt::kSplitMultiUnits)), "alloc split tickets");
+  TRY(cudaMemsetAsync(c->split_ticket, 0, size_t(tt::kSplitMultiUnits) * sizeof(unsigned), s),
+      "clear split tickets");
   {
     size_t nd = size_t(c->n_dom), Dz = size_t(D);
     TRY(dalloc(&c->out_th, nd * Dz), "alloc search output");

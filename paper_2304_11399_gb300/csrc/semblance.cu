@@ -46,12 +46,17 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
     fn = pick(sk::kKindSplit, a, mv);
     if (!fn) return cudaErrorInvalidValue;
     const long long units = (n + 63) / 64;
-    const int S = sk::split_warps(units);
+    int S = sk::split_warps(units);
+    b.split_blocks = 1;
+    if (units <= kSplitMultiUnits && a.split_part && a.split_ticket) {
+      S = sk::kSplitMaxWarps;
+      b.split_blocks = sk::split_blocks(units);
+    }
     const size_t smem = sk::split_smem_bytes(S, a.W);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(sk::split_smem_bytes(sk::kSplitMaxWarps, a.W)));
     if (e != cudaSuccess) return e;
-    fn<<<unsigned(units), 32 * S, smem, s>>>(b);
+    fn<<<unsigned(units * b.split_blocks), 32 * S, smem, s>>>(b);
     return cudaGetLastError();
   } else if (a.kernel == TT_KERNEL_SCALAR) {
     fn = pick(sk::kKindScalar, a, mv);

@@ -392,14 +392,17 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
   store_S(a, q1, L1.d, normalise<T>(Q.y, N, E.y, Ed1));
 }
 
-// K1 for small launches (few 64-pair units): a block of S warps shares one
-// unit, warp w walking the w-th contiguous slice of every pair's aperture;
-// the slices' partial sums meet in shared memory and are added in slice
-// order. S (8, 16 or 32, the block's warp count) grows as the launch shrinks
-// so that the GPU holds about 152 x 32 warps. The summation order (per
-// slice, then across slices) depends on S and differs from the
-// one-warp-per-unit kernel, so both are chosen by launch size alone -- every
-// variant of a launch runs the same kernel -- and results stay reproducible.
+// K1 for small launches (few 64-pair units): B blocks of S warps share one
+// unit, warp w of block b walking slice b S + w of the B S contiguous slices
+// of every pair's aperture. Within a block the slices' partial sums meet in
+// shared memory and are added in slice order; with B > 1 each block writes
+// its sums to global scratch and the last block of the unit to arrive (an
+// atomic ticket, no waiting) adds the B block sums in block order. S (8, 16
+// or 32, the block's warp count) and B (1 to 4) grow as the launch shrinks,
+// so that the GPU stays busy. The summation order depends on (S, B) and
+// differs from the one-warp-per-unit kernel, so all are chosen by launch
+// size alone -- every variant of a launch runs the same code -- and results
+// stay reproducible.
 constexpr int kSplitWarps = 8;       // S for the largest split launches
 constexpr int kSplitMaxWarps = 32;
 static_assert(TT_SPLIT_MAX_PAIRS % 64 == 0, "split threshold is counted in 64-pair units");
@@ -411,6 +414,22 @@ inline int split_warps(long long units) {
   if (units * 8 >= target) return 8;
   if (units * 16 >= target) return 16;
   return kSplitMaxWarps;
+}
+
+// blocks per unit (1..kSplitMaxBlocks) for a split launch of `units` units at
+// S = 32 (one block per SM): the fewest waves per unit of work, ceil(units B /
+// 152) / B, smallest B on ties
+inline int split_blocks(long long units) {
+  int best = 1;
+  double cost = double((units + 151) / 152);
+  for (int B = 2; B <= kSplitMaxBlocks; ++B) {
+    const double c = double((units * B + 151) / 152) / B;
+    if (c < cost) {
+      cost = c;
+      best = B;
+    }
+  }
+  return best;
 }
 
 // dynamic shared memory of a split block: FP64 energies [S][64], FP32
@@ -428,15 +447,17 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps) k_semblance_split(const E
   float* part_E = reinterpret_cast<float*>(part_Ed + S * 64);  // [S][64]
   float* part_s = part_E + S * 64;                             // [S][64][K]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long unit = blockIdx.x;
+  const int B = a.split_blocks;
+  const long long unit = blockIdx.x / B;
+  const int part = int(blockIdx.x - unit * B);
   const long long q0 = unit * 64 + lane, q1 = q0 + 32;
   Lane L0, L1;
   const bool v0 = lane_setup<OP>(a, q0, L0);
   const bool v1 = lane_setup<OP>(a, q1, L1);
   auto slice = [&](const Lane& L, int& r0, int& r1) {
-    const long long n = L.e1 - L.e0;
-    r0 = L.e0 + int(n * w / S);
-    r1 = L.e0 + int(n * (w + 1) / S);
+    const long long n = L.e1 - L.e0, nsl = (long long)S * B, sl = (long long)part * S + w;
+    r0 = L.e0 + int(n * sl / nsl);
+    r1 = L.e0 + int(n * (sl + 1) / nsl);
   };
   if (v0 && v1 && same_aperture(L0, L1)) {
     int r0, r1;
@@ -476,24 +497,61 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps) k_semblance_split(const E
     }
   }
   __syncthreads();
-  if (threadIdx.x < 64) {
-    const int p = threadIdx.x;
-    Lane L;
-    if (!lane_setup<OP>(a, unit * 64 + p, L)) return;
-    float Q = 0.f, E = 0.f;
-    double Ed = 0.0;
+  // the block's sums of pair p = threadIdx.x (< 64), slices in order
+  const int p = threadIdx.x;
+  Lane L;
+  const bool valid = p < 64 && lane_setup<OP>(a, unit * 64 + p, L);
+  float sk[K];
+  float E = 0.f;
+  double Ed = 0.0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      float sk = 0.f;
-      for (int v = 0; v < S; ++v) sk = __fadd_rn(sk, part_s[(v * 64 + p) * K + k]);
-      Q = fmaf(sk, sk, Q);
-    }
+  for (int k = 0; k < K; ++k) sk[k] = 0.f;
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      for (int v = 0; v < S; ++v) sk[k] = __fadd_rn(sk[k], part_s[(v * 64 + p) * K + k]);
     for (int v = 0; v < S; ++v) {
       E = __fadd_rn(E, part_E[v * 64 + p]);
       Ed += part_Ed[v * 64 + p];
     }
-    store_S(a, unit * 64 + p, L.d, normalise<T>(Q, L.e1 - L.e0, E, Ed));
   }
+  if (B > 1) {
+    // publish the block's sums; the unit's last block adds them in block order
+    const size_t set = size_t(unit) * B + part;
+    float* gp = a.split_part + (set * 64 + p) * kSplitPartStride;
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) gp[k] = sk[k];
+      gp[K] = E;
+      a.split_part_d[set * 64 + p] = Ed;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int last;
+    if (threadIdx.x == 0) last = atomicAdd(a.split_ticket + unit, 1u) == unsigned(B - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) a.split_ticket[unit] = 0u;  // ready for the next launch
+    if (!valid) return;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sk[k] = 0.f;
+    E = 0.f;
+    Ed = 0.0;
+    for (int b = 0; b < B; ++b) {
+      const size_t sb = size_t(unit) * B + b;
+      const float* q = a.split_part + (sb * 64 + p) * kSplitPartStride;
+#pragma unroll
+      for (int k = 0; k < K; ++k) sk[k] = __fadd_rn(sk[k], __ldcg(q + k));
+      E = __fadd_rn(E, __ldcg(q + K));
+      Ed += __ldcg(a.split_part_d + sb * 64 + p);
+    }
+  }
+  if (!valid) return;
+  float Q = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) Q = fmaf(sk[k], sk[k], Q);
+  store_S(a, unit * 64 + p, L.d, normalise<T>(Q, L.e1 - L.e0, E, Ed));
 }
 
 // K1, grid-mapped (queue == nullptr: one 64-pair unit per warp, the grid

@@ -15,6 +15,13 @@ namespace tt {
 // parameters per operator: CMP (C), CRS (A, B, C), FO-CRS (Am, Ah, Bmm, Bmh, Bhh)
 constexpr int op_dim(int op) { return op == TT_OP_CMP ? 1 : op == TT_OP_CRS ? 3 : 5; }
 
+// Split launches of at most kSplitMultiUnits units may spread a unit over up
+// to kSplitMaxBlocks blocks; their partial sums need this scratch.
+constexpr int kSplitMultiUnits = 304;
+constexpr int kSplitMaxBlocks = 4;
+constexpr int kSplitPartSets = kSplitMultiUnits * kSplitMaxBlocks;
+constexpr int kSplitPartStride = 2 * 8 + 2;  // floats per pair: K + 1 for the widest window
+
 // Padded trace layout: sample n of trace r lives at r * pitch + kPadFront + n.
 // kPadFront >= max half window; kPadBack >= 2 * max half window + 2 so that a
 // window whose position is clamped to ns + w reads only padding zeros.
@@ -43,6 +50,10 @@ struct EvalArgs {
   int kernel;               // TT_KERNEL_PACKED / _PERSISTENT / _SCALAR (forward launches)
   int block;                // threads per block: 128 or 256
   int split;                // 1: small forward launches split the aperture over warps
+  int split_blocks;         // blocks per unit of a split launch (set by the launcher)
+  float* split_part;        // [kSplitPartSets][64][K + 1] block partial sums (s_k, E)
+  double* split_part_d;     // [kSplitPartSets][64] block partial FP64 energies
+  unsigned* split_ticket;   // [kSplitMultiUnits] arrivals per unit, zero between launches
   unsigned long long* queue;  // persistent mode: work-unit counter, zero at launch
 };
 
@@ -176,6 +187,9 @@ struct tt_ctx {
         *pol_bS = nullptr;
   int* d_err = nullptr;     // device-side validation flag
   unsigned long long* queue = nullptr;  // persistent-kernel work counter
+  float* split_part = nullptr;          // multi-block split scratch (tt::kSplitPartSets sets)
+  double* split_part_d = nullptr;
+  unsigned* split_ticket = nullptr;
   // launch configuration (tt_ctx_set_option / tt_ctx_autotune)
   int kernel = TT_KERNEL_PACKED, block = 256;
   bool split = true;  // TT_OPT_SPLIT
