@@ -314,12 +314,12 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, storage=args.storage,
                            device=dev)
-    tuned = None
-    if args.workload == "batched":
-        th = torch.empty((prob.n_dom, wl.de.np, ctx.D), dtype=torch.float32, device=dev)
-        tt.tt_de_step(ctx, 0, th)
-        tuned = {f"{k}/{b}": round(v, 3) for (k, b), v in tt.tt_ctx_autotune(ctx, th).items()}
-        del th
+    # pick the kernel variant and block size on a generation-0 population
+    # (every variant gives the same bits, so this changes speed only)
+    th = torch.empty((prob.n_dom, wl.de.np, ctx.D), dtype=torch.float32, device=dev)
+    tt.tt_de_step(ctx, 0, th)
+    tuned = {f"{k}/{b}": round(v, 3) for (k, b), v in tt.tt_ctx_autotune(ctx, th).items()}
+    del th
     best_t = torch.empty((prob.n_dom, ctx.D), dtype=torch.float32, device=dev)
     best_s = torch.empty((prob.n_dom,), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 18, dtype=torch.float32, device=dev)  # 256 MiB
@@ -433,6 +433,8 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "comparison": comparison}
         if tuned:
             line["config"]["autotune_ms"] = tuned
+            line["config"]["kernel"] = (f"{tt.tt_ctx_get_option(ctx, 'kernel')}/"
+                                        f"{tt.tt_ctx_get_option(ctx, 'block')}")
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

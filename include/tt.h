@@ -263,8 +263,9 @@ typedef struct tt_ens_cfg {
 } tt_ens_cfg;
 
 /* Run the ENS sweep over the context's (m0, t0) grid (n_m0 * n_t0 == n_dom)
- * with F, CR, seed and bounds from the context's tt_de_cfg, whose np must be
- * at least np_f and np_bf (both >= 4). Writes best_theta [n_dom][D] and
+ * with F, CR, seed, bounds and adapt from the context's tt_de_cfg (with
+ * adapt, every estimated sample starts a fresh JADE memory and archive),
+ * whose np must be at least np_f and np_bf (both >= 4). Writes best_theta [n_dom][D] and
  * best_S [n_dom]; *n_evals (host, may be NULL) receives the semblance-call
  * count of eq. ens_semblance for the estimated and interpolated samples
  * actually visited. Uses the context's search scratch (not concurrently with
