@@ -387,6 +387,13 @@ def main():
                 "per_launch_ms": stats["semblance_ms"] / stats["timed_launches"],
                 "trace_evals_per_s": stats["trace_evals"] / (stats["semblance_ms"] / 1e3),
                 "semblance_share_of_step": stats["semblance_ms"] / ms}
+        # the on-chip bound: each pair moves 2w+2 samples through the L1 data
+        # path, 128 B per clock per SM
+        w = int(prob.half_window)
+        bytes_pair = (2 * w + 2) * (2 if args.storage == "bf16" else 4)
+        l1_peak = SM_COUNT * 128.0 * SM_MAX_MHZ * 1e6 / bytes_pair
+        roof["l1"] = {"bytes_per_pair": bytes_pair, "peak_pairs_per_s": l1_peak,
+                      "frac": roof["trace_evals_per_s"] / l1_peak}
     # the same search in other forms on the same GPU (rank 0, line workload)
     comparison = None
     if rank == 0 and args.workload == "line" and not args.no_compare:
