@@ -46,6 +46,9 @@ def workload_config(wl, n_gpus):
     if wl.info is not None:
         name = (f"{p.n_groups} uneven CRS problems, 16-240 traces and 750-3000 samples "
                 f"(dt 2/4 ms) each, every sample a domain, window 11")
+    elif wl.storage == "bf16" and p.n_m0 and wl.line is not None and wl.line.n_cmp == 2000:
+        name = (f"large line 2000 CMP x 120 offsets x 2000 samples (dt 2 ms, BF16-stored), "
+                f"aperture +-25 CMP, window 11, central {p.n_m0}-CMP slab solved")
     elif p.op == 2:
         name = ("FO-CRS on the common-offset section at h0 = 1000 m of the 200-CMP x 48 x "
                 "1500-sample line (dt 4 ms), aperture +-8 CMP x +-1000 m, window 11")
@@ -272,10 +275,12 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--cmps", type=int, default=0,
                     help="solve only the first CMPS midpoints of the line (profiling case)")
-    ap.add_argument("--workload", default="line", choices=["line", "batched", "fo"],
+    ap.add_argument("--workload", default="line", choices=["line", "batched", "fo", "large"],
                     help="line: the 200-CMP CRS line (default); batched: 4096 uneven CRS "
                          "problems (every sample a domain, DE 64 x 80, autotuned kernel); fo: "
-                         "FO-CRS on the line's common-offset section at 1000 m")
+                         "FO-CRS on the line's common-offset section at 1000 m; large: the "
+                         "2000-CMP x 120 x 2000 BF16-stored line, a central slab of --cmps "
+                         "CMPs (default 100) solved")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -294,8 +299,14 @@ def main():
     import paper_2304_11399_gb300 as tt
     from synth import configs
 
-    wl = {"line": configs.crs_line, "batched": configs.batched,
-          "fo": configs.fo_panel}[args.workload](rank)
+    if args.workload == "large":
+        n_slab = args.cmps or 100
+        c0 = 1000 - n_slab // 2
+        wl = configs.large_line(rank, cmps=list(range(c0, c0 + n_slab)))
+        args.storage = "bf16"
+    else:
+        wl = {"line": configs.crs_line, "batched": configs.batched,
+              "fo": configs.fo_panel}[args.workload](rank)
     wl.storage = args.storage
     if args.cmps and args.workload == "line":
         import synth
