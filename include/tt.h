@@ -326,7 +326,7 @@ tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
  *                 events between streams). 0: never split.
  *  Changing an option drops a captured graph. */
 enum { TT_OPT_KERNEL = 1, TT_OPT_BLOCK = 2, TT_OPT_SEARCH_GRAPH = 3, TT_OPT_SPLIT = 4 };
-#define TT_SPLIT_MAX_PAIRS (152 * 8 * 64)
+#define TT_SPLIT_MAX_PAIRS (152 * 32 * 64)
 enum { TT_KERNEL_PACKED = 1, TT_KERNEL_PERSISTENT = 2, TT_KERNEL_SCALAR = 3 };
 #define TT_N_TUNE_CANDIDATES 6
 tt_status tt_ctx_set_option(tt_ctx* ctx, int32_t option, int64_t value);
