@@ -23,13 +23,15 @@
  *    asynchronous launch. tt_last_error() gives a message.
  *  - A context may be used from one host thread at a time; calls on
  *    different streams that share a context's scratch (tt_search,
- *    tt_neighbor_exchange) must not overlap.
+ *    tt_ens_search, tt_neighbor_exchange, tt_polish, split evaluations --
+ *    see TT_OPT_SPLIT) must not overlap.
  *
  * Notation (the paper's): a domain is one zero-offset sample (m0, it0),
  * t0 = it0 dt (Sec. 2.1, "index-vector point (t, tr)"); its aperture is the
  * set of N traces used by one semblance call (T_a in eq. order); theta is a
- * parameter vector ("individual", Sec. 2) of D = 1 (CMP: C) or D = 3
- * (ZO-CRS: A, B, C) values; NP individuals form a domain's population.
+ * parameter vector ("individual", Sec. 2) of D = 1 (CMP: C), D = 3
+ * (ZO-CRS: A, B, C) or D = 5 (FO-CRS: Am, Ah, Bmm, Bmh, Bhh) values; NP
+ * individuals form a domain's population.
  */
 #ifndef TT_H
 #define TT_H
