@@ -155,3 +155,48 @@ def test_full_line_search_recovers_parameters():
                     and abs(bt[d, 2] - truth[3]) <= 0.01 * truth[3])
     assert tried >= 3
     assert hits >= max(3, int(0.8 * tried))
+
+
+@pytest.mark.slow
+def test_full_line_search_in_the_bench_configuration():
+    """The 200-CMP x 48 x 1500 line at full size (300,000 domains, DE 64 x
+    100, exchange every 10, 5 polish steps), with the kernel variant chosen
+    by the autotuner as the bench does: call count, the oracle reproducing
+    the reported S at 300 sampled domains, and recovery of the recentred
+    (A, C) within 1% at event-centred samples of isolated strong events."""
+    wl = configs.crs_line(0)
+    prob, line = wl.problem, wl.line
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, device=dev())
+    th0 = torch.empty((prob.n_dom, 64, 3), dtype=torch.float32, device=dev())
+    tt.tt_de_step(ctx, 0, th0)
+    tt.tt_ctx_autotune(ctx, th0)
+    del th0
+    bt, bs, n = tt.tt_search(ctx)
+    bt, bs = bt.cpu().numpy(), bs.cpu().numpy()
+    ctx.close()
+    edges = 2 * (prob.n_m0 * (prob.n_t0 - 1) + prob.n_t0 * (prob.n_m0 - 1))
+    assert n == oracle.counts.search_calls(prob.n_dom, 64, 100, 10 * edges, 5)
+    doms = np.sort(np.random.default_rng(11).choice(prob.n_dom, 300, replace=False))
+    ref = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, prob, bt[doms][:, None, :],
+                                          domains=doms)[:, 0]
+    assert np.max(np.abs(ref - bs[doms])) <= 1e-5
+    lo, hi = np.array(wl.de.lo), np.array(wl.de.hi)
+    hits = tried = 0
+    ev = line.events
+    for e in range(len(ev)):
+        c = int(np.argmin(np.abs(line.cmp_x - ev[e, 0])))
+        if c < 15 or c > line.n_cmp - 16 or abs(ev[e, 5]) < 0.7:
+            continue
+        truth = synth.crs_recentre(ev[e], line.cmp_x[c])
+        if truth is None or not (lo[0] < truth[1] < hi[0] and lo[2] < truth[3] < hi[2]):
+            continue
+        it = int(round(truth[0] / wl.dt))
+        others = [synth.crs_recentre(ev[k], line.cmp_x[c]) for k in range(len(ev)) if k != e]
+        if it < 20 or it > prob.n_t0 - 20 or any(o is not None and abs(o[0] - truth[0]) < 0.1
+                                                 for o in others):
+            continue
+        d = c * prob.n_t0 + it
+        tried += 1
+        hits += int(abs(bt[d, 0] - truth[1]) <= 0.01 * (hi[0] - lo[0])
+                    and abs(bt[d, 2] - truth[3]) <= 0.01 * truth[3])
+    assert tried >= 5 and hits == tried, (hits, tried)

@@ -173,6 +173,7 @@ def test_full_line_sampled_outputs():
     g = torch.Generator(device=dev()).manual_seed(9)
     theta_t.copy_(lo + torch.rand(theta_t.shape, generator=g, device=dev()) * (hi - lo))
     ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, None, device=dev())
+    tt.tt_ctx_autotune(ctx, theta_t)  # the bench's launch configuration
     S = tt.tt_semblance_eval(ctx, theta_t).cpu().numpy()
     ctx.close()
     theta = theta_t.cpu().numpy()
