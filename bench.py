@@ -119,16 +119,15 @@ def recovery(wl, best_theta, tol=0.01):
     return {"within_1pct": hits, "of": tried}
 
 
-def fo_recovery(wl, best_theta, tol=0.01):
+def fo_recovery(wl, best_theta):
     """FO-CRS: event-centred samples (CMPs within 40 m of an isolated strong
-    event's midpoint) whose two slopes and offset curvatures (Am, Ah, Bmh,
-    Bhh) are within ``tol`` of their bound ranges of the exact re-expansion
-    about (m0, h0); Bmm is weakly constrained by a +-100 m midpoint aperture."""
+    event's midpoint) whose two slopes (Am, Ah) are within 1% and 5% of their
+    bound ranges of the exact re-expansion about (m0, h0)."""
     import synth
     prob, line = wl.problem, wl.line
     lo, hi = np.array(wl.de.lo), np.array(wl.de.hi)
     h0 = float(prob.group_h0[0])
-    hits = tried = 0
+    h1 = h5 = tried = 0
     ev = line.events
     for e in range(len(ev)):
         others = np.delete(ev[:, 1], e)
@@ -145,9 +144,10 @@ def fo_recovery(wl, best_theta, tol=0.01):
                 continue
             d = c * prob.n_t0 + it
             tried += 1
-            hits += int(all(abs(best_theta[d, k] - p[1 + k]) <= tol * (hi[k] - lo[k])
-                            for k in (0, 1, 3, 4)))
-    return {"within_1pct": hits, "of": tried}
+            err = max(abs(best_theta[d, k] - p[1 + k]) / (hi[k] - lo[k]) for k in (0, 1))
+            h1 += int(err <= 0.01)
+            h5 += int(err <= 0.05)
+    return {"slopes_within_1pct": h1, "slopes_within_5pct": h5, "of": tried}
 
 
 # ------------------------------------------------------------------ paper comparison
