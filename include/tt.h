@@ -316,11 +316,12 @@ tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
  *  TT_OPT_SPLIT   1 (default): a forward evaluation of fewer than
  *                 TT_SPLIT_MAX_PAIRS (domain, vector) pairs -- too few to fill
  *                 the GPU at one warp per 64 pairs -- runs a kernel in which
- *                 the 8 warps of a block share 64 pairs, each warp summing a
- *                 contiguous eighth of every pair's aperture, the eight partial
- *                 sums added in order; every variant then launches that kernel,
- *                 so S still does not depend on TT_OPT_KERNEL / TT_OPT_BLOCK,
- *                 but its rounding differs from the unsplit kernels' (both stay
+ *                 the S warps of a block (8, 16 or 32, more for smaller
+ *                 launches) share 64 pairs, each warp summing a contiguous
+ *                 slice of every pair's aperture, the partial sums added in
+ *                 slice order; every variant then launches that kernel, so S
+ *                 still does not depend on TT_OPT_KERNEL / TT_OPT_BLOCK, but
+ *                 its rounding differs from the unsplit kernels' (all stay
  *                 within 1e-5 of the exact semblance). The smallest launches
  *                 also spread a unit over up to 4 blocks that combine their
  *                 sums through the context's scratch, so split evaluations on

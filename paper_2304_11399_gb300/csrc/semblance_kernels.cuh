@@ -403,7 +403,6 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
 // differs from the one-warp-per-unit kernel, so all are chosen by launch
 // size alone -- every variant of a launch runs the same code -- and results
 // stay reproducible.
-constexpr int kSplitWarps = 8;       // S for the largest split launches
 constexpr int kSplitMaxWarps = 32;
 static_assert(TT_SPLIT_MAX_PAIRS % 64 == 0, "split threshold is counted in 64-pair units");
 constexpr long long kSplitMaxUnits = TT_SPLIT_MAX_PAIRS / 64;
