@@ -439,6 +439,8 @@ def main():
         l1_peak = SM_COUNT * 128.0 * SM_MAX_MHZ * 1e6 / bytes_pair
         roof["l1"] = {"bytes_per_pair": bytes_pair, "peak_pairs_per_s": l1_peak,
                       "frac": roof["trace_evals_per_s"] / l1_peak}
+        # semblance trace-samples per second: pairs x window length
+        roof["trace_samples_per_s"] = roof["trace_evals_per_s"] * (2 * w + 1)
     # the same search in other forms on the same GPU (rank 0, line workload)
     comparison = None
     if rank == 0 and args.workload == "line" and not args.no_compare:
