@@ -319,7 +319,8 @@ void free_ctx(tt_ctx* c) {
                   c->dom_it0, c->dom_group, c->bounds, c->pop, c->fit, c->trial[0],
                   c->trial[1], c->tfit[0], c->tfit[1], c->snap, c->imports, c->slots,
                   c->best_idx, c->pol_th, c->pol_g, c->pol_S, c->pol_bth, c->pol_bS, c->d_err,
-                  c->queue, c->split_part, c->split_part_d, c->split_ticket, c->out_th,
+                  c->queue, c->split_part, c->split_part_d, c->split_ticket, c->split_part2,
+                  c->split_part_d2, c->split_ticket2, c->out_th,
                   c->out_S, c->jade_mu, c->jade_arc, c->jade_F,
                   c->jade_CR, c->jade_na};
   for (void* p : ptrs)
@@ -327,6 +328,9 @@ void free_ctx(tt_ctx* c) {
   for (auto e : c->ev) cudaEventDestroy(e);
   tt_ctx_drop_graph(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  for (cudaEvent_t e : c->side_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 
@@ -571,6 +575,12 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
   TRY(dalloc(&c->split_part_d, size_t(tt::kSplitPartSets) * 64), "alloc split scratch");
   TRY(dalloc(&c->split_ticket, size_t(tt::kSplitMultiUnits)), "alloc split tickets");
   TRY(cudaMemsetAsync(c->split_ticket, 0, size_t(tt::kSplitMultiUnits) * sizeof(unsigned), s),
+      "clear split tickets");
+  TRY(dalloc(&c->split_part2, size_t(tt::kSplitPartSets) * 64 * tt::kSplitPartStride),
+      "alloc split scratch");
+  TRY(dalloc(&c->split_part_d2, size_t(tt::kSplitPartSets) * 64), "alloc split scratch");
+  TRY(dalloc(&c->split_ticket2, size_t(tt::kSplitMultiUnits)), "alloc split tickets");
+  TRY(cudaMemsetAsync(c->split_ticket2, 0, size_t(tt::kSplitMultiUnits) * sizeof(unsigned), s),
       "clear split tickets");
   {
     size_t nd = size_t(c->n_dom), Dz = size_t(D);

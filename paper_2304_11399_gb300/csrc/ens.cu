@@ -195,10 +195,31 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
     stages[n_st++] = {true, -1, e.n_skip == 0 ? 0 : 1};
     stages[n_st++] = {true, +1, e.n_skip};
   }
+  // The interpolated samples of a step (interpolate, evaluate, keep) only
+  // touch that trace's skipped samples, which the next steps of the stage do
+  // not read; they run on the side stream, overlapping the next step, with
+  // their maps and buffers double-buffered by step parity and their own
+  // split scratch. A step waits for the side work of the step two before it
+  // (which used the same buffers); every stage ends with a join.
+  if (!c->side_stream) {
+    cudaError_t r = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
+    for (int k = 0; r == cudaSuccess && k < 4; ++k)
+      r = cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming);
+    if (r != cudaSuccess) return tt_cuda_check(c, r, "side stream");
+  }
+  cudaStream_t s2 = c->side_stream;
+  cudaEvent_t* fork_ev = c->side_ev;      // [parity]: main -> side
+  cudaEvent_t* join_ev = c->side_ev + 2;  // [parity]: side work of that parity done
+  bool side_busy[2] = {false, false};
   int* map_est = c->best_idx;
-  int* map_skp = c->slots;
-  float* th_skp = c->imports;
-  float* S_skp = c->snap;
+  int* map_skp2[2] = {c->slots, c->slots + c->n_dom};
+  float* th_skp2[2] = {c->imports, c->imports + size_t(c->n_dom) * D};
+  float* S_skp2[2] = {c->pol_S, c->pol_bS};
+  auto join = [&](int par) -> cudaError_t {
+    if (!side_busy[par]) return cudaSuccess;
+    side_busy[par] = false;
+    return cudaStreamWaitEvent(s, join_ev[par], 0);
+  };
   const uint32_t key0 = uint32_t(c->cfg.seed & 0xffffffffull), key1 = uint32_t(c->cfg.seed >> 32);
   for (int si = 0; si < n_st; ++si) {
     const Stage& sg = stages[si];
@@ -219,6 +240,11 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
       int active = 0;  // traces of this step (buckets long enough)
       for (int b = 0; b < n_buckets; ++b) active += g.tb < std::min(nb, n_m0 - b * nb);
       if (active == 0) continue;
+      const int par = step & 1;
+      STEP(join(par), "ens join");
+      int* map_skp = map_skp2[par];
+      float* th_skp = th_skp2[par];
+      float* S_skp = S_skp2[par];
       k_ens_maps<<<blocks(std::max(n_est_loc, n_skp_loc)), 256, 0, s>>>(g, map_est, map_skp);
       STEP(c->counted(cudaGetLastError()), "ens maps");
       if (g.n_est > 0) {
@@ -270,18 +296,27 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
         STEP(c->counted(cudaGetLastError()), "ens update");
       }
       if (g.n_skp > 0 && g.n_est > 0) {
-        k_ens_interp<<<blocks(n_skp_loc), 256, 0, s>>>(g, D, map_skp, bth, th_skp);
+        STEP(cudaEventRecord(fork_ev[par], s), "ens fork");
+        STEP(cudaStreamWaitEvent(s2, fork_ev[par], 0), "ens fork");
+        k_ens_interp<<<blocks(n_skp_loc), 256, 0, s2>>>(g, D, map_skp, bth, th_skp);
         STEP(c->counted(cudaGetLastError()), "ens interpolate");
         tt::EvalArgs ei = c->eval_args(th_skp, 1, S_skp);
         ei.n_dom = n_skp_loc;
         ei.dom_map = map_skp;
-        STEP(c->semblance(ei, s, false), "ens evaluate interpolated");
+        ei.split_part = c->split_part2;
+        ei.split_part_d = c->split_part_d2;
+        ei.split_ticket = c->split_ticket2;
+        STEP(c->semblance(ei, s2, false), "ens evaluate interpolated");
         calls += (unsigned long long)active * g.n_skp;
-        k_ens_keep<<<blocks(n_skp_loc), 256, 0, s>>>(n_skp_loc, D, map_skp, th_skp, S_skp, bth,
-                                                     bS);
+        k_ens_keep<<<blocks(n_skp_loc), 256, 0, s2>>>(n_skp_loc, D, map_skp, th_skp, S_skp, bth,
+                                                      bS);
         STEP(c->counted(cudaGetLastError()), "ens keep");
+        STEP(cudaEventRecord(join_ev[par], s2), "ens join");
+        side_busy[par] = true;
       }
     }
+    STEP(join(0), "ens join");
+    STEP(join(1), "ens join");
   }
 #undef STEP
   *n_calls = calls;

@@ -190,6 +190,13 @@ struct tt_ctx {
   float* split_part = nullptr;          // multi-block split scratch (tt::kSplitPartSets sets)
   double* split_part_d = nullptr;
   unsigned* split_ticket = nullptr;
+  // a second split scratch and a side stream: the ENS sweep evaluates each
+  // step's interpolated samples concurrently with the next step
+  float* split_part2 = nullptr;
+  double* split_part_d2 = nullptr;
+  unsigned* split_ticket2 = nullptr;
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t side_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // launch configuration (tt_ctx_set_option / tt_ctx_autotune)
   int kernel = TT_KERNEL_PACKED, block = 256;
   bool split = true;  // TT_OPT_SPLIT
