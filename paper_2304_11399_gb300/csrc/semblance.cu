@@ -49,8 +49,8 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
     int S = sk::split_warps(units);
     b.split_blocks = 1;
     if (units <= kSplitMultiUnits && a.split_part && a.split_ticket) {
-      S = sk::kSplitMaxWarps;
-      b.split_blocks = sk::split_blocks(units);
+      S = sk::kSplitMultiWarps;
+      b.split_blocks = kSplitMaxBlocks;
     }
     const size_t smem = sk::split_smem_bytes(S, a.W);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,

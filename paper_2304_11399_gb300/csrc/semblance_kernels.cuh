@@ -397,39 +397,27 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
 // of every pair's aperture. Within a block the slices' partial sums meet in
 // shared memory and are added in slice order; with B > 1 each block writes
 // its sums to global scratch and the last block of the unit to arrive (an
-// atomic ticket, no waiting) adds the B block sums in block order. S (8, 16
-// or 32, the block's warp count) and B (1 to 4) grow as the launch shrinks,
-// so that the GPU stays busy. The summation order depends on (S, B) and
+// atomic ticket, no waiting) adds the B block sums in block order. (S, B)
+// is (8 or 16, 1) for mid-size launches and (16, 4) for the smallest, so
+// that the GPU stays busy. The summation order depends on (S, B) and
 // differs from the one-warp-per-unit kernel, so all are chosen by launch
 // size alone -- every variant of a launch runs the same code -- and results
 // stay reproducible.
-constexpr int kSplitMaxWarps = 32;
+constexpr int kSplitMaxWarps = 16;
 static_assert(TT_SPLIT_MAX_PAIRS % 64 == 0, "split threshold is counted in 64-pair units");
 constexpr long long kSplitMaxUnits = TT_SPLIT_MAX_PAIRS / 64;
 
-// warps per unit for a split launch of `units` 64-pair units
-inline int split_warps(long long units) {
-  const long long target = 152ll * 32;
-  if (units * 8 >= target) return 8;
-  if (units * 16 >= target) return 16;
-  return kSplitMaxWarps;
-}
+// warps per block of a one-block-per-unit split launch of `units` units:
+// 8 once that keeps about 152 x 32 warps resident, else 16
+inline int split_warps(long long units) { return units * 8 >= 152ll * 32 ? 8 : kSplitMaxWarps; }
 
-// blocks per unit (1..kSplitMaxBlocks) for a split launch of `units` units at
-// S = 32 (one block per SM): the fewest waves per unit of work, ceil(units B /
-// 152) / B, smallest B on ties
-inline int split_blocks(long long units) {
-  int best = 1;
-  double cost = double((units + 151) / 152);
-  for (int B = 2; B <= kSplitMaxBlocks; ++B) {
-    const double c = double((units * B + 151) / 152) / B;
-    if (c < cost) {
-      cost = c;
-      best = B;
-    }
-  }
-  return best;
-}
+// Launches of at most kSplitMultiUnits units run kSplitMultiWarps warps per
+// block and kSplitMaxBlocks blocks per unit: 64 slices per aperture in
+// 512-thread blocks, two of which share an SM, so one block's barrier overlaps
+// the other's loads. The best of the (S, B) pairs timed on ENS sweeps
+// (S x B = 64 with 512- or 256-thread blocks; 1024-thread blocks were 12-20%
+// slower).
+constexpr int kSplitMultiWarps = 16;
 
 // dynamic shared memory of a split block: FP64 energies [S][64], FP32
 // energies [S][64], stack sums [S][64][K]
@@ -438,7 +426,7 @@ inline size_t split_smem_bytes(int S, int W) {
 }
 
 template <int OP, int W, typename T, bool MV>
-__global__ void __launch_bounds__(32 * kSplitMaxWarps) k_semblance_split(const EvalArgs a) {
+__global__ void __launch_bounds__(32 * kSplitMaxWarps, 2) k_semblance_split(const EvalArgs a) {
   constexpr int K = 2 * W + 1;
   extern __shared__ __align__(16) unsigned char split_smem[];
   const int S = blockDim.x >> 5;

@@ -53,10 +53,10 @@ def batch():
 
 @pytest.mark.parametrize("P", [1, 4, 20, 64, 130])
 def test_variants_bit_identical_on_a_line(P):
-    """2400 domains: P = 1 and 4 split the aperture over 32 warps per unit
-    (P = 1 over several blocks per unit), P = 20 and 64 over 8, P = 130
-    (4875 units) is too large to split; the oracle checks a sample of
-    domains for the two largest P."""
+    """2400 domains: P = 1 and 4 split the aperture over 4 blocks of 16
+    warps per unit, P = 20 (750 units) and 64 (2400 units) over 8 warps,
+    P = 130 (4875 units) is too large to split; the oracle checks a sample
+    of domains for the two largest P."""
     wl = small_line(31)
     theta = random_theta(wl.problem.n_dom, P, wl.de.lo, wl.de.hi, P)
     doms = np.arange(wl.problem.n_dom)
