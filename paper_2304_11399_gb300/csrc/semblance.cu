@@ -48,9 +48,14 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
     const long long units = (n + 63) / 64;
     int S = sk::split_warps(units);
     b.split_blocks = 1;
-    if (units <= kSplitMultiUnits && a.split_part && a.split_ticket) {
-      S = sk::kSplitMultiWarps;
-      b.split_blocks = kSplitMaxBlocks;
+    if (a.split_part && a.split_ticket) {
+      if (units <= kSplitSmallUnits) {
+        S = sk::kSplitMultiWarps;
+        b.split_blocks = kSplitMaxBlocks;
+      } else if (units < kSplitMultiUnits) {
+        S = 8;
+        b.split_blocks = 2;
+      }
     }
     const size_t smem = sk::split_smem_bytes(S, a.W);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -398,8 +398,8 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
 // shared memory and are added in slice order; with B > 1 each block writes
 // its sums to global scratch and the last block of the unit to arrive (an
 // atomic ticket, no waiting) adds the B block sums in block order. (S, B)
-// is (8 or 16, 1) for mid-size launches and (16, 4) for the smallest, so
-// that the GPU stays busy. The summation order depends on (S, B) and
+// is (16, 4) up to 304 units, (8, 2) below 1824 and (8, 1) above, so that
+// the GPU stays busy. The summation order depends on (S, B) and
 // differs from the one-warp-per-unit kernel, so all are chosen by launch
 // size alone -- every variant of a launch runs the same code -- and results
 // stay reproducible.
@@ -411,12 +411,14 @@ constexpr long long kSplitMaxUnits = TT_SPLIT_MAX_PAIRS / 64;
 // 8 once that keeps about 152 x 32 warps resident, else 16
 inline int split_warps(long long units) { return units * 8 >= 152ll * 32 ? 8 : kSplitMaxWarps; }
 
-// Launches of at most kSplitMultiUnits units run kSplitMultiWarps warps per
+// Launches of at most kSplitSmallUnits units run kSplitMultiWarps warps per
 // block and kSplitMaxBlocks blocks per unit: 64 slices per aperture in
 // 512-thread blocks, two of which share an SM, so one block's barrier overlaps
 // the other's loads. The best of the (S, B) pairs timed on ENS sweeps
 // (S x B = 64 with 512- or 256-thread blocks; 1024-thread blocks were 12-20%
-// slower).
+// slower). Below kSplitMultiUnits units, (8, 2): timed 17% faster than
+// (8, 1) on the 938-unit launches of an ENS 30 x 30 sweep, while from about
+// 2500 units (ENS 80 x 80) one block per unit is best.
 constexpr int kSplitMultiWarps = 16;
 
 // dynamic shared memory of a split block: FP64 energies [S][64], FP32

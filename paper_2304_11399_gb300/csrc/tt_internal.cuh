@@ -15,11 +15,15 @@ namespace tt {
 // parameters per operator: CMP (C), CRS (A, B, C), FO-CRS (Am, Ah, Bmm, Bmh, Bhh)
 constexpr int op_dim(int op) { return op == TT_OP_CMP ? 1 : op == TT_OP_CRS ? 3 : 5; }
 
-// Split launches of at most kSplitMultiUnits units may spread a unit over up
-// to kSplitMaxBlocks blocks; their partial sums need this scratch.
-constexpr int kSplitMultiUnits = 304;
+// Split launches of fewer than kSplitMultiUnits units spread a unit over
+// several blocks (4 up to kSplitSmallUnits units, else 2); their partial
+// sums need this scratch.
+constexpr int kSplitSmallUnits = 304;
+constexpr int kSplitMultiUnits = 1824;
 constexpr int kSplitMaxBlocks = 4;
-constexpr int kSplitPartSets = kSplitMultiUnits * kSplitMaxBlocks;
+constexpr int kSplitPartSets = kSplitMultiUnits * 2 > kSplitSmallUnits * kSplitMaxBlocks
+                                   ? kSplitMultiUnits * 2
+                                   : kSplitSmallUnits * kSplitMaxBlocks;
 constexpr int kSplitPartStride = 2 * 8 + 2;  // floats per pair: K + 1 for the widest window
 
 // Padded trace layout: sample n of trace r lives at r * pitch + kPadFront + n.

@@ -54,7 +54,8 @@ def batch():
 @pytest.mark.parametrize("P", [1, 4, 20, 64, 130])
 def test_variants_bit_identical_on_a_line(P):
     """2400 domains: P = 1 and 4 split the aperture over 4 blocks of 16
-    warps per unit, P = 20 (750 units) and 64 (2400 units) over 8 warps,
+    warps per unit, P = 20 (750 units) over 2 blocks of 8 warps, P = 64
+    (2400 units) over one block of 8 warps,
     P = 130 (4875 units) is too large to split; the oracle checks a sample
     of domains for the two largest P."""
     wl = small_line(31)
