@@ -156,8 +156,8 @@ def paper_compare(tt, wl, dev, stream, runs=None, recover=None):
     """The paper's own experiment (Sec. 5.2-5.3, Fig. rms_coherence and
     ens_jade_execution_time) on this line: JADE (the plain search with the
     adaptation of F and CR and the archive, mu starting at 0.5, no exchange
-    or polish) at 5x1, 30x30 and 80x80 against the ENS sweep at 5x1 and 80x80
-    (NP_bf 5, NG_bf 1, N_skip 2, N_cycle 1, buckets of 64 traces).
+    or polish) at 5x1, 30x30 and 80x80 against the ENS sweep at 5x1, 30x30
+    and 80x80 (NP_bf 5, NG_bf 1, N_skip 2, N_cycle 1, buckets of 64 traces).
     Each search runs once untimed (graph capture) and once timed; quality is
     the RMS of the coherence panel (the paper's g-type measure) and the
     recovery of event-centred parameters."""
@@ -166,7 +166,7 @@ def paper_compare(tt, wl, dev, stream, runs=None, recover=None):
     out = {}
     runs = runs or (("jade_5x1", "jade", 5, 1), ("jade_30x30", "jade", 30, 30),
                     ("jade_80x80", "jade", 80, 80), ("ens_5x1", "ens", 5, 1),
-                    ("ens_80x80", "ens", 80, 80))
+                    ("ens_30x30", "ens", 30, 30), ("ens_80x80", "ens", 80, 80))
     recover = recover or recovery
     for label, kind, npop, ngen in runs:
         de = copy.copy(wl.de)
@@ -195,6 +195,9 @@ def paper_compare(tt, wl, dev, stream, runs=None, recover=None):
                       "recovery": recover(wl, th.cpu().numpy())}
         ctx.close()
     out["jade_30x30_over_ens_5x1_time"] = out["jade_30x30"]["seconds"] / out["ens_5x1"]["seconds"]
+    if "ens_30x30" in out:
+        out["jade_30x30_over_ens_30x30_time"] = (out["jade_30x30"]["seconds"] /
+                                                 out["ens_30x30"]["seconds"])
     if "ens_80x80" in out:
         out["jade_80x80_over_ens_80x80_time"] = (out["jade_80x80"]["seconds"] /
                                                  out["ens_80x80"]["seconds"])
