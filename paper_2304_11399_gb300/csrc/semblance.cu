@@ -42,7 +42,8 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
     fn = pick(sk::kKindGrad, a, mv);
     blocks = (n + block - 1) / block;
   } else if (a.split && (n + 63) / 64 < kSplitMaxUnits) {
-    // few units: a block per unit, the aperture split over its warps
+    // too few units to fill the GPU: each unit's aperture split over the
+    // warps of B blocks, (S, B) by launch size only
     fn = pick(sk::kKindSplit, a, mv);
     if (!fn) return cudaErrorInvalidValue;
     const long long units = (n + 63) / 64;
