@@ -184,3 +184,23 @@ def test_full_batched_workload():
     ref = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, prob, bt[doms][:, None, :],
                                           domains=doms)[:, 0]
     assert np.max(np.abs(ref - bs[doms])) <= 1e-5
+
+
+@pytest.mark.slow
+def test_full_batched_workload_sampled_outputs():
+    """The 4096-problem batched workload at full size (7.6M domains), NP = 64
+    random vectors at every domain in the launch configuration the bench
+    times (autotuned variant): 300 sampled domains recomputed by the oracle."""
+    wl = configs.batched(0)
+    prob = wl.problem
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, device=dev())
+    th = torch.empty((prob.n_dom, 64, 3), dtype=torch.float32, device=dev())
+    tt.tt_de_step(ctx, 0, th)
+    tt.tt_ctx_autotune(ctx, th)
+    S = tt.tt_semblance_eval(ctx, th).cpu().numpy()
+    ctx.close()
+    doms = np.sort(np.random.default_rng(5).choice(prob.n_dom, 300, replace=False))
+    theta = th[torch.as_tensor(doms, device=dev())].cpu().numpy()
+    ref = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, prob, theta, domains=doms)
+    assert np.max(np.abs(S[doms] - ref)) <= 1e-5
+    assert np.all((S >= 0) & (S <= 1 + 1e-6))

@@ -80,3 +80,26 @@ def test_bf16_slab_search(slab):
             hits += int(abs(bt[d, 0] - truth[1]) <= 0.01 * (hi[0] - lo[0])
                         and abs(bt[d, 2] - truth[3]) <= 0.01 * truth[3])
     assert tried >= 4 and hits >= 0.75 * tried, (hits, tried)
+
+
+@pytest.mark.slow
+def test_bench_slab_sampled_outputs():
+    """The bench's large-line case: the central 100-CMP slab of the full
+    2000-CMP line (BF16-stored, aperture +-25 CMPs), NP = 96 random vectors
+    at every domain, autotuned variant; 200 sampled domains recomputed by the
+    oracle on the BF16-rounded record."""
+    wl = configs.large_line(0, cmps=list(range(950, 1050)))
+    prob = wl.problem
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, storage="bf16", device=dev())
+    th = torch.empty((prob.n_dom, 96, 3), dtype=torch.float32, device=dev())
+    tt.tt_de_step(ctx, 0, th)
+    tt.tt_ctx_autotune(ctx, th)
+    S = tt.tt_semblance_eval(ctx, th).cpu().numpy()
+    ctx.close()
+    doms = np.sort(np.random.default_rng(6).choice(prob.n_dom, 200, replace=False))
+    theta = th[torch.as_tensor(doms, device=dev())].cpu().numpy()
+    idx = np.unique(prob.ap_idx)
+    rounded = wl.traces.copy()
+    rounded[idx] = bf16_round(wl.traces[idx])
+    ref = oracle.semblance.semblance_many(rounded, wl.mid, wl.off, prob, theta, domains=doms)
+    assert np.max(np.abs(S[doms] - ref)) <= 1e-5
