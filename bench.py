@@ -297,6 +297,33 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU leg
 
+def l2_probe(dev, stream):
+    """L2 bandwidth probe: device-to-device copies between two buffers that
+    together fit in L2, timed with CUDA events after warm-up; the largest
+    read + write rate over three sizes. The semblance kernel's own L2 traffic
+    is small (L1 serves ~99% of its loads), so this bounds nothing on the
+    line: it places the L2 level next to the L1 and HBM figures."""
+    best = 0.0
+    for mib in (8, 16, 24):
+        n = mib << 18
+        a = torch.ones(n, dtype=torch.float32, device=dev)
+        b = torch.empty_like(a)
+        with torch.cuda.stream(stream):
+            for _ in range(10):
+                b.copy_(a)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 100
+            e0.record(stream)
+            for _ in range(reps):
+                b.copy_(a)
+            e1.record(stream)
+        e1.synchronize()
+        best = max(best, 2 * n * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        del a, b
+    return {"gbs": best, "method": "torch copy_ between two L2-resident buffers (2 x 8-24 MiB), "
+                                   "100 reps, read + write bytes"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,6 +471,8 @@ def main():
                       "frac": roof["trace_evals_per_s"] / l1_peak}
         # semblance trace-samples per second: pairs x window length
         roof["trace_samples_per_s"] = roof["trace_evals_per_s"] * (2 * w + 1)
+        if rank == 0:
+            roof["l2_probe"] = l2_probe(dev, stream)
     # the same search in other forms on the same GPU (rank 0, line workload)
     comparison = None
     if rank == 0 and args.workload == "line" and not args.no_compare:
