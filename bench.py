@@ -297,31 +297,50 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU leg
 
+# DRAM bytes (read + write) of one generation launch of K1 on the CRS line,
+# packed/128, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean of three launches, caches flushed by ncu before each):
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:k_semblance -s 40 -c 3
+#       python bench.py --steps 1 --warmup 0 --no-e2e --no-cpu-baseline --no-compare
+# 297.9 MB read + 61.2 MB written: the compulsory bytes (theta 230.4 MB and the
+# 57.6 MB line read, S 76.8 MB written, part of it still in L2 when the launch
+# ends), no re-reads.
+K1_LINE_DRAM_BYTES = 297_862_059 + 61_190_827
+K1_LINE_DRAM_KERNEL = "packed/128"
+
+
 def l2_probe(dev, stream):
     """L2 bandwidth probe: device-to-device copies between two buffers that
-    together fit in L2, timed with CUDA events after warm-up; the largest
-    read + write rate over three sizes. The semblance kernel's own L2 traffic
-    is small (L1 serves ~99% of its loads), so this bounds nothing on the
-    line: it places the L2 level next to the L1 and HBM figures."""
+    together fit in L2, 20 copies captured in a CUDA graph (no launch gaps
+    from the host), replayed after warm-up and timed with CUDA events; the
+    largest read + write rate over three sizes. The semblance kernel's own L2
+    traffic is small (L1 serves ~99% of its loads), so this bounds nothing on
+    the line: it places the L2 level next to the L1 and HBM figures."""
+    import torch
     best = 0.0
-    for mib in (8, 16, 24):
+    for mib in (16, 24, 32):
         n = mib << 18
         a = torch.ones(n, dtype=torch.float32, device=dev)
         b = torch.empty_like(a)
+        b.copy_(a)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(20):
+                b.copy_(a)
         with torch.cuda.stream(stream):
-            for _ in range(10):
-                b.copy_(a)
+            g.replay()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 100
             e0.record(stream)
-            for _ in range(reps):
-                b.copy_(a)
+            for _ in range(5):
+                g.replay()
             e1.record(stream)
         e1.synchronize()
-        best = max(best, 2 * n * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
-        del a, b
-    return {"gbs": best, "method": "torch copy_ between two L2-resident buffers (2 x 8-24 MiB), "
-                                   "100 reps, read + write bytes"}
+        best = max(best, 2 * n * 4 * 100 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        del g, a, b
+    return {"gbs": best, "method": "torch copy_ between two L2-resident buffers (2 x 16-32 MiB), "
+                                   "20 copies per CUDA graph, 5 replays, read + write bytes"}
 
 
 def main():
@@ -456,8 +475,11 @@ def main():
         flops = stats["trace_evals"] * FLOPS_PER_TRACE_EVAL[int(prob.op)]
         n_l = stats["semblance_launches"]
         achieved = (flops / n_l) / (stats["semblance_ms"] / stats["timed_launches"] / 1e3) / 1e12
+        kern = f"{tt.tt_ctx_get_option(ctx, 'kernel')}/{tt.tt_ctx_get_option(ctx, 'block')}"
+        traffic = (K1_LINE_DRAM_BYTES if (args.workload == "line" and args.storage == "f32" and
+                                          not args.cmps and kern == K1_LINE_DRAM_KERNEL) else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_semblance (FP32 FMA pipe; peak = 152 SM x 128 lanes x 2 x 2070 MHz)",
                 "per_launch_ms": stats["semblance_ms"] / stats["timed_launches"],
                 "trace_evals_per_s": stats["trace_evals"] / (stats["semblance_ms"] / 1e3),
