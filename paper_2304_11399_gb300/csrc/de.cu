@@ -239,6 +239,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_de_step(const DeArgs a) {
   // (ii) best = argmax, lowest index on ties
   const int b = warp_argmax(sfit, NP, lane);
   if (lane == 0 && a.best_idx) a.best_idx[d] = b;
+  if (a.ens_best_th) {
+    if (lane < D) a.ens_best_th[(size_t)gd * D + lane] = spop[b * D + lane];
+    if (lane == 0) a.ens_best_S[gd] = sfit[b];
+  }
   if (!a.next) return;
   // (iii) DE/current-to-best/1/bin + JADE bound repair, one rounding per op;
   // adaptive: per-member F_i, CR_i and r2 over population + archive

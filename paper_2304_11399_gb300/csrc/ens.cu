@@ -12,14 +12,15 @@
 //
 // GPU mapping: the sweep is sequential over the traces of a bucket, so one
 // step handles the current trace of every bucket at once -- all estimated
-// samples of all buckets in each launch. Per step: build the local-to-global
-// domain maps on the device, seed and initialise the populations, evaluate,
-// run the DE generations (the ordinary DE and semblance kernels on the mapped
-// subset), write the bests, interpolate the skipped samples, evaluate them
-// and keep the higher. Random numbers: Philox keyed by the global domain,
-// with the counter's generation field (stage + 1) * 65536 + g. Scratch: the
-// context's search buffers (the context's NP must be at least NP_f and
-// NP_bf). The whole sweep is captured into a CUDA graph on first use.
+// samples of all buckets in each launch. Per step: seed and initialise the
+// populations (the same kernel writes the step's local-to-global domain map),
+// evaluate, run the DE generations (the ordinary DE and semblance kernels on
+// the mapped subset; the last selection also writes the bests), interpolate
+// the skipped samples (writing their map), evaluate them and keep the higher.
+// Random numbers: Philox keyed by the global domain, with the counter's
+// generation field (stage + 1) * 65536 + g. Scratch: the context's search
+// buffers (the context's NP must be at least NP_f and NP_bf). The whole
+// sweep is captured into a CUDA graph on first use.
 #include <algorithm>
 
 #include "tt_internal.cuh"
@@ -59,21 +60,12 @@ __device__ __forceinline__ int skip_domain(const StepGeo& g, int r) {
   return (b * g.nb + g.tb) * g.n_t0 + t;
 }
 
-__global__ void k_ens_maps(StepGeo g, int* map_est, int* map_skp) {
-  const int n1 = g.n_buckets * g.n_est, n2 = g.n_buckets * g.n_skp;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < max(n1, n2);
-       r += gridDim.x * blockDim.x) {
-    if (r < n1) map_est[r] = est_domain(g, r);
-    if (r < n2) map_skp[r] = skip_domain(g, r);
-  }
-}
-
 __device__ __forceinline__ bool unset(const float* th) { return isnan(th[0]); }
 
 // One thread per (local domain r, population slot i): the i-th present seed
 // in the order (t-1, t+1, previous trace, own best) -- only the previous
 // trace in the exploration stage -- or a random member drawn from Philox.
-__global__ void k_ens_init(StepGeo g, int bf, int NP, int D, const int* map, const float* best_th,
+__global__ void k_ens_init(StepGeo g, int bf, int NP, int D, int* map, const float* best_th,
                            float* pop, uint32_t key0, uint32_t key1, uint32_t gen,
                            const float* lo, const float* hi, float* jade_mu, int* jade_na,
                            float F0, float CR0) {
@@ -81,7 +73,8 @@ __global__ void k_ens_init(StepGeo g, int bf, int NP, int D, const int* map, con
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const int r = int(q / NP), i = int(q - (long long)r * NP);
-  const int d = map[r];
+  const int d = est_domain(g, r);
+  if (i == 0) map[r] = d;  // the step's map for the kernels that follow
   if (d < 0) return;
   if (jade_mu && i == 0) {  // a fresh JADE memory and an empty archive per sample
     jade_mu[2 * (size_t)r] = CR0;
@@ -127,11 +120,11 @@ __global__ void k_ens_update(int n, int NP, int D, const int* map, const float* 
 // Linear interpolation in t of each skipped sample between the bests of the
 // nearest estimated samples of its trace (FP32, one rounding per operation);
 // beyond the first or last estimated sample the nearest one is copied.
-__global__ void k_ens_interp(StepGeo g, int D, const int* map, const float* best_th,
-                             float* th_out) {
+__global__ void k_ens_interp(StepGeo g, int D, int* map, const float* best_th, float* th_out) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= g.n_buckets * g.n_skp) return;
-  const int d = map[r];
+  const int d = skip_domain(g, r);
+  map[r] = d;  // the map of the evaluation and keep that follow
   if (d < 0) return;
   const int t = d % g.n_t0, row = d - t;
   const int ta = t >= g.init ? g.init + ((t - g.init) / g.stride) * g.stride : -1;
@@ -245,8 +238,6 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
       int* map_skp = map_skp2[par];
       float* th_skp = th_skp2[par];
       float* S_skp = S_skp2[par];
-      k_ens_maps<<<blocks(std::max(n_est_loc, n_skp_loc)), 256, 0, s>>>(g, map_est, map_skp);
-      STEP(c->counted(cudaGetLastError()), "ens maps");
       if (g.n_est > 0) {
         const uint32_t gen0 = uint32_t(si + 1) * 65536u;
         k_ens_init<<<blocks((long long)n_est_loc * NP), 256, 0, s>>>(
@@ -289,11 +280,14 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
           a.fit = c->fit;
           a.trial = c->trial[cur ^ 1];
           a.tfit = c->tfit[cur ^ 1];
+          a.ens_best_th = bth;  // the bests written by the selecting kernel
+          a.ens_best_S = bS;
           STEP(c->counted(tt::launch_de_step(a, s)), "ens select");
+        } else {
+          k_ens_update<<<blocks((long long)n_est_loc * 32), 256, 0, s>>>(
+              n_est_loc, NP, D, map_est, c->pop, c->fit, bth, bS);
+          STEP(c->counted(cudaGetLastError()), "ens update");
         }
-        k_ens_update<<<blocks((long long)n_est_loc * 32), 256, 0, s>>>(
-            n_est_loc, NP, D, map_est, c->pop, c->fit, bth, bS);
-        STEP(c->counted(cudaGetLastError()), "ens update");
       }
       if (g.n_skp > 0 && g.n_est > 0) {
         STEP(cudaEventRecord(fork_ev[par], s), "ens fork");

@@ -87,6 +87,10 @@ struct DeArgs {
   float* jade_arc;          // [n_dom][NP][D] archived parents
   float* jade_F;            // [n_dom][NP] F_i of the pending trial
   float* jade_CR;           // [n_dom][NP] CR_i of the pending trial
+  // ENS (optional): after the selection the population's best theta and S
+  // go to [global id][D] / [global id] of the sweep's best panel
+  float* ens_best_th;
+  float* ens_best_S;
 };
 
 cudaError_t launch_de_step(const DeArgs& a, cudaStream_t s);
