@@ -118,3 +118,20 @@ def test_ens_beats_jade_at_equal_cost():
     ctx.close()
     assert abs(n_e - n_j) / n_j < 0.15
     assert float(np.sqrt(np.mean(S_e ** 2))) > 1.5 * float(np.sqrt(np.mean(S_j ** 2)))
+
+
+@pytest.mark.slow
+def test_full_line_sweep_in_the_bench_configuration():
+    """The sweep the bench times on the full CRS line (300,000 domains,
+    NP 5 x NG 1 both ways, N_skip 2, N_cycle 1, buckets of 64 traces):
+    call count, every sample reached, and the reported S equal to the
+    oracle's at the reported parameters on 300 sampled domains."""
+    wl = configs.crs_line(0)
+    prob = wl.problem
+    th, S, n = _gpu(wl, E(n_bucket=64))
+    assert n == oracle.counts.ens_calls(prob.n_dom, 5, 1, 5, 1, 2, 1)
+    assert not np.any(np.isnan(th)) and np.all((S >= 0) & (S <= 1 + 1e-6))
+    doms = np.sort(np.random.default_rng(8).choice(prob.n_dom, 300, replace=False))
+    ref = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, prob, th[doms][:, None, :],
+                                          domains=doms)[:, 0]
+    assert np.max(np.abs(ref - S[doms])) <= 1e-5

@@ -103,3 +103,28 @@ def test_bench_slab_sampled_outputs():
     rounded[idx] = bf16_round(wl.traces[idx])
     ref = oracle.semblance.semblance_many(rounded, wl.mid, wl.off, prob, theta, domains=doms)
     assert np.max(np.abs(S[doms] - ref)) <= 1e-5
+
+
+@pytest.mark.slow
+def test_whole_line_one_launch_sampled_outputs():
+    """The largest configuration in one launch: all 4,000,000 domains of the
+    2000-CMP BF16 line (up to 6120 traces each), NP = 96 random vectors,
+    384M pairs and 2.3e12 trace evaluations; 100 sampled domains recomputed
+    by the oracle on the BF16-rounded record."""
+    wl = configs.large_line(0)
+    prob = wl.problem
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, storage="bf16", device=dev())
+    th = torch.empty((prob.n_dom, 96, 3), dtype=torch.float32, device=dev())
+    tt.tt_de_step(ctx, 0, th)
+    S = tt.tt_semblance_eval(ctx, th).cpu().numpy()
+    ctx.close()
+    assert np.all((S >= 0) & (S <= 1 + 1e-6))
+    doms = np.sort(np.random.default_rng(9).choice(prob.n_dom, 100, replace=False))
+    theta = th[torch.as_tensor(doms, device=dev())].cpu().numpy()
+    del th
+    idx = np.unique(np.concatenate([prob.ap_idx[prob.ap_ptr[g]:prob.ap_ptr[g + 1]]
+                                    for g in np.unique(prob.dom_group[doms])]))
+    rounded = np.zeros_like(wl.traces)
+    rounded[idx] = bf16_round(wl.traces[idx])
+    ref = oracle.semblance.semblance_many(rounded, wl.mid, wl.off, prob, theta, domains=doms)
+    assert np.max(np.abs(S[doms] - ref)) <= 1e-5
