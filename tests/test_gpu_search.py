@@ -3,7 +3,7 @@ of the reported semblance with the oracle, and recovery of the generating
 parameters at event-centred domains.
 
 Search trajectories of the FP32 GPU path and the FP64 oracle part once two
-semblance values differ below 1e-5, so end-to-end parity is judged by the
+semblance values differ below 1e-5, so end-to-end parity is assessed by the
 recovered parameters (within 1% of the generating values: relative for C,
 a fraction of the bound range for A) and by re-evaluating the reported
 optimum with the oracle; step-level parity is bit-exact (test_gpu_de).
