@@ -310,6 +310,18 @@ K1_LINE_DRAM_BYTES = 297_862_059 + 61_190_827
 K1_LINE_DRAM_KERNEL = "packed/128"
 
 
+def hbm_peak_gbs():
+    """The measured HBM copy bandwidth of this GPU model (MEASURED_PEAKS.json
+    at the repository root), else the fallback figure of an earlier GB300
+    measurement."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def l2_probe(dev, stream):
     """L2 bandwidth probe: device-to-device copies between two buffers that
     together fit in L2, 20 copies captured in a CUDA graph (no launch gaps
@@ -493,6 +505,12 @@ def main():
                       "frac": roof["trace_evals_per_s"] / l1_peak}
         # semblance trace-samples per second: pairs x window length
         roof["trace_samples_per_s"] = roof["trace_evals_per_s"] * (2 * w + 1)
+        # the gathered samples as a byte rate, beside the HBM copy bandwidth:
+        # L1 serves them, at several times what HBM could deliver
+        hbm, src = hbm_peak_gbs()
+        gathered = roof["trace_evals_per_s"] * bytes_pair / 1e9
+        roof["gathered"] = {"gbs": gathered, "hbm_gbs": hbm, "hbm_source": src,
+                            "over_hbm": gathered / hbm}
         if rank == 0:
             roof["l2_probe"] = l2_probe(dev, stream)
     # the same search in other forms on the same GPU (rank 0, line workload)
