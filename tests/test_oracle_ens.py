@@ -15,7 +15,8 @@ import dataclasses
 import numpy as np
 import pytest
 
-from oracle import counts, ens, search as osearch
+from oracle import counts, de, ens, search as osearch
+from oracle.semblance import semblance_many
 import synth
 from synth import configs
 
@@ -107,3 +108,44 @@ def test_ens_beats_jade_at_equal_cost_and_recovers(adapt):
             tried += 1
             hits += int(abs(th_e[d, 2] - tr[3]) <= 0.05 * tr[3])
     assert tried >= 8 and hits >= 0.6 * tried, (hits, tried)
+
+
+def test_exploration_carries_each_bucket_first_trace():
+    """With one member and no generations the exploration stage is pure
+    propagation (Sec. 3.4, previous-trace seed): the first trace of each
+    bucket draws a random member per sample (keyed by its own domain, slot 0,
+    the stage's generation code), and every later trace of the bucket starts
+    from -- and keeps -- the best of the same sample on the previous trace.
+    Buckets do not exchange anything (Sec. 4)."""
+    wl = configs.crs_line(1, n_cmp=7, ns=60, n_events=2, ap_half=2, tau_max=0.22)
+    prob = wl.problem
+    cfg = EnsCfg(np=1, ng=0, n_skip=0, n_cycle=0, n_bucket=3)
+    th, S, n = ens.ens_search(wl.traces, wl.mid, wl.off, prob, cfg)
+    n_t0 = prob.n_t0
+    assert n == prob.n_dom  # one call per sample, nothing interpolated
+    lo, hi = np.asarray(cfg.lo, f32), np.asarray(cfg.hi, f32)
+    for c0 in (0, 3, 6):  # buckets [0, 1, 2], [3, 4, 5], [6]
+        for t in range(n_t0):
+            first = de.init_individual(cfg.seed, c0 * n_t0 + t, 0, lo, hi,
+                                       gen=ens.gen_code(0, 0))
+            for c in range(c0, min(c0 + 3, 7)):
+                np.testing.assert_array_equal(th[c * n_t0 + t], first)
+    # the reported S is the semblance of the carried member at each sample
+    doms = np.arange(0, prob.n_dom, 7)
+    ref = semblance_many(wl.traces, wl.mid, wl.off, prob, th[doms][:, None, :],
+                         domains=doms)[:, 0]
+    np.testing.assert_array_equal(S[doms], ref.astype(f32))
+
+
+def test_cycles_never_lower_a_sample():
+    """Backward-and-forward cycles seed every estimated sample with its own
+    best among the four seeds (Sec. 3.4), selection is elitist and an
+    interpolated value replaces a best only when higher (Sec. 3.5), so the
+    semblance of every sample after the cycles is at least its value after
+    the exploration stage -- and the cycles raise many of them."""
+    wl = configs.crs_line(3, n_cmp=8, ns=60, n_events=3, ap_half=2, tau_max=0.2, snr=6.0)
+    prob = wl.problem
+    _, S_x, _ = ens.ens_search(wl.traces, wl.mid, wl.off, prob, EnsCfg(n_cycle=0, n_bucket=4))
+    _, S_c, _ = ens.ens_search(wl.traces, wl.mid, wl.off, prob, EnsCfg(n_cycle=2, n_bucket=4))
+    assert np.all(S_c >= S_x)
+    assert np.mean(S_c > S_x) > 0.3
