@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import counts, de, exchange as ex, search as osearch
-from oracle.semblance import semblance
+from oracle.semblance import semblance, semblance_many
 import synth
 from synth import configs
 
@@ -147,3 +147,79 @@ def test_crs_search_with_exchange_counts_and_recovery():
     assert abs(th[d, 0] - truth[1]) <= 0.01 * (hi[0] - lo[0])
     assert th[d, 2] == pytest.approx(truth[3], rel=0.01)
     assert S[d] > 0.5
+
+
+def test_exchange_result_is_the_best_of_own_and_neighbours_bests():
+    """With the exchange as the last step (NG = exch_every, no polish), every
+    sample's result is the best of its own pre-exchange best and the
+    neighbours' pre-exchange bests evaluated at it: the imports replace
+    members other than the own best (Sec. 3.4). The pre-exchange bests are
+    those of the same search without exchange (same draws up to that point).
+    Pins the snapshot (the bests, taken before any import), the cadence (after
+    generation exch_every's selection) and the import count."""
+    base = configs.crs_line(2, n_cmp=5, ns=80, n_events=2, ap_half=1, np_=8, ng=3,
+                            exch_every=3, polish_steps=0, tau_max=0.28)
+    prob = synth.line_problem(base.line, half_window=3, ap_half=1, cmps=[1, 2, 3],
+                              t0_range=(30, 34))
+    assert (prob.n_m0, prob.n_t0) == (3, 4)
+    th_x, S_x, n_x = osearch.search(base.traces, base.mid, base.off, prob, base.de)
+    de0 = configs.DEConfig(**{**vars(base.de), "exch_every": 0})
+    th_0, S_0, n_0 = osearch.search(base.traces, base.mid, base.off, prob, de0)
+    n_imports = 2 * (3 * 3 + 4 * 2)
+    assert n_x - n_0 == n_imports
+    for d in range(prob.n_dom):
+        nb = ex.neighbours(d, prob.n_m0, prob.n_t0)
+        s_imp = semblance_many(base.traces, base.mid, base.off, prob,
+                               th_0[nb][None].astype(f32), domains=[d])[0].astype(f32)
+        assert S_x[d] == max(f32(S_0[d]), *s_imp), d
+
+
+def test_polish_ascends_by_the_scaled_gradient():
+    """One polish step from a point below the peak moves by
+    lr (hi - lo)^2 dS/dtheta, the gradient taken here by central differences
+    of the FP64 semblance (independent of the adjoint), and raises S; five
+    steps get strictly closer to the generating velocity."""
+    wl = configs.cmp_search(0)
+    x = wl.traces.astype(np.float64)
+    ev = wl.line.events[0]
+    t0 = int(round(ev[1] / wl.dt)) * wl.dt
+    C = ev[4]
+    lo, hi = np.array(wl.de.lo), np.array(wl.de.hi)
+    dm, h = np.zeros(48), wl.off.astype(float)
+    start = np.array([C * 1.02])
+    S0 = semblance(x, wl.dt, dm, h, t0, 0, start, 5)
+    eps = 1e-4 * C
+    g_fd = (semblance(x, wl.dt, dm, h, t0, 0, start + eps, 5) -
+            semblance(x, wl.dt, dm, h, t0, 0, start - eps, 5)) / (2 * eps)
+    th1, S1, n1 = osearch.polish_point(x, wl.dt, dm, h, t0, 0, 5, start, lo, hi, 1,
+                                       wl.de.polish_lr)
+    assert n1 == 2 and S1 > S0
+    step = wl.de.polish_lr * (hi - lo) ** 2 * g_fd
+    assert th1[0] - start[0] == pytest.approx(step[0], rel=1e-3)
+    th5, S5, _ = osearch.polish_point(x, wl.dt, dm, h, t0, 0, 5, start, lo, hi, 5,
+                                      wl.de.polish_lr)
+    assert S5 > S0 and abs(th5[0] - C) < abs(start[0] - C)
+
+
+def test_polish_keeps_the_best_iterate():
+    """A step size far too large throws every later iterate to the bounds,
+    where the coherence is lower: the polish returns the starting point and
+    its semblance (it never lowers S)."""
+    wl = configs.cmp_search(0)
+    x = wl.traces.astype(np.float64)
+    ev = wl.line.events[0]
+    t0 = int(round(ev[1] / wl.dt)) * wl.dt
+    C = ev[4]
+    lo, hi = np.array(wl.de.lo), np.array(wl.de.hi)
+    dm, h = np.zeros(48), wl.off.astype(float)
+    start = np.array([C * 1.02])
+    S0 = semblance(x, wl.dt, dm, h, t0, 0, start, 5)
+    lr = wl.de.polish_lr * 1e6
+    eps = 1e-4 * C
+    g_fd = (semblance(x, wl.dt, dm, h, t0, 0, start + eps, 5) -
+            semblance(x, wl.dt, dm, h, t0, 0, start - eps, 5)) / (2 * eps)
+    th1 = np.clip(start + lr * (hi - lo) ** 2 * g_fd, lo, hi)
+    assert th1[0] in (lo[0], hi[0])
+    assert semblance(x, wl.dt, dm, h, t0, 0, th1, 5) < S0  # the first step overshoots
+    th, S, n = osearch.polish_point(x, wl.dt, dm, h, t0, 0, 5, start, lo, hi, 3, lr)
+    assert n == 4 and S == S0 and np.array_equal(th, start)
