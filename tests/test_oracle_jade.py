@@ -78,8 +78,28 @@ def test_cr_draws_clip_at_the_normal_tail():
     assert np.all((CR >= 0) & (CR <= 1))
     tail = 1 - scipy_stats.norm.cdf(0.5)   # P(0.95 + 0.1 z > 1)
     assert abs(np.mean(CR == 1) - tail) < 0.015
+    # and at the lower end: CR_i = 0 with the mass of the tail below 0
+    CR0 = np.array([jade.draw_cr(4, 1, 3, i, f32(0.05)) for i in range(20000)])
+    low = scipy_stats.norm.cdf(-0.5)        # P(0.05 + 0.1 z < 0)
+    assert abs(np.mean(CR0 == 0) - low) < 0.015
+    assert np.all((CR0 >= 0) & (CR0 <= 1))
     assert jade.cr_threshold_f32(f32(1.0)) == 1 << 24
     assert jade.cr_threshold_f32(f32(0.0)) == 0
+
+
+def test_normal_draw_is_the_first_polar_variate():
+    """Marsaglia's polar method on the first accepted pair (v1, v2) of the
+    member's words gives two normals, v1 sqrt(-2 ln s / s) and
+    v2 sqrt(-2 ln s / s); the draw is the first. Recomputed here in FP64 from
+    the pair (the FP32 logarithm and square root agree to a few ulp)."""
+    for i in range(300):
+        for v1, v2, s in jade._pairs(7, 3, jade.TAG_NORMAL | 5, i, jade.NORMAL_TRIES):
+            if s < 1:
+                q = -2.0 * math.log(float(s)) / float(s)
+                z1 = float(v1) * math.sqrt(q)
+                break
+        z = float(jade.normal_draw(7, 3, 5, i))
+        assert abs(z - z1) <= 2e-6 * max(1.0, abs(z1)), (i, z, z1)
 
 
 def test_memory_update_hand_values():
