@@ -327,3 +327,26 @@ def test_gradient_zero_at_exact_maximum():
     S, g = osm.semblance_grad(x, dt, np.zeros(30), h, t0, CMP, [C], w)
     assert S == pytest.approx(1.0)
     assert g[0] == pytest.approx(0.0, abs=1e-6 / C)
+
+
+def test_gradient_at_zero_traveltime():
+    """At t0 = 0 a zero-offset trace at the reference midpoint has T = 0 for
+    every parameter vector: its amplitudes do not move, so it adds nothing to
+    the gradient (and no 0/0), while the other traces do. The gradient stays
+    finite and matches central differences."""
+    rng = np.random.default_rng(8)
+    dt, w = 0.004, 3
+    x = rng.standard_normal((12, 200))
+    dm = np.concatenate([[0.0], rng.uniform(-100, 100, 11)])
+    h = np.concatenate([[0.0], rng.uniform(200, 2000, 11)])
+    th = np.array([1e-4, 2e-8, 1 / 2500 ** 2])
+    assert osm.traveltime_sq(CRS, th, 0.0, dm, h)[0] == 0.0
+    S, g = osm.semblance_grad(x, dt, dm, h, 0.0, CRS, th, w)
+    assert np.all(np.isfinite(g))
+    for d, step in ((0, 1e-9), (2, 1e-12)):
+        p, m = th.copy(), th.copy()
+        p[d] += step
+        m[d] -= step
+        fd = (osm.semblance(x, dt, dm, h, 0.0, CRS, p, w)
+              - osm.semblance(x, dt, dm, h, 0.0, CRS, m, w)) / (2 * step)
+        assert fd == pytest.approx(g[d], rel=1e-4, abs=1e-6 * abs(g).max()), (d, fd, g[d])
