@@ -77,3 +77,23 @@ def test_ctx_create_rejects_on_the_host(lib, name, breaks, status, msg):
     assert st == status, (name, st, lib.tt_last_error(None))
     assert msg in lib.tt_last_error(None), lib.tt_last_error(None)
     assert not h.value
+
+
+NULL_CTX_CALLS = [n for n, (res, _) in _lib.SIGNATURES.items()
+                  if res is not None and n not in ("tt_last_error", "tt_version",
+                                                   "tt_ctx_create", "tt_semblance_eval_noalloc")]
+
+
+@pytest.mark.parametrize("name", NULL_CTX_CALLS)
+def test_every_entry_point_rejects_a_null_context(lib, name):
+    """Called with a NULL context (every other argument zero or NULL), each
+    entry point returns TT_ERR_INVALID_ARG with a message, touching nothing."""
+    _, argtypes = _lib.SIGNATURES[name]
+    args = [None if (t is _lib.P or hasattr(t, "contents")) else 0 for t in argtypes]
+    st = getattr(lib, name)(*args)
+    assert st == INV, (name, st)
+    assert lib.tt_last_error(None)
+
+
+def test_destroy_accepts_null(lib):
+    lib.tt_ctx_destroy(None)
