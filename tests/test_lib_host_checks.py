@@ -97,3 +97,36 @@ def test_every_entry_point_rejects_a_null_context(lib, name):
 
 def test_destroy_accepts_null(lib):
     lib.tt_ctx_destroy(None)
+
+
+NOALLOC_CASES = [
+    ("NULL structs", None, INV, b"NULL"),
+    ("BF16 storage", lambda g, p: setattr(g, "storage", 1), INV, b"F32"),
+    ("FO-CRS", lambda g, p: setattr(p, "op", 2), UNS, b""),
+    ("operator", lambda g, p: setattr(p, "op", 9), INV, b"op must be"),
+    ("half window", lambda g, p: setattr(p, "half_window", 9), UNS, b"half_window 9"),
+    ("negative size", lambda g, p: setattr(p, "n_dom", -1), INV, b"negative size"),
+    ("NULL problem array", lambda g, p: setattr(p, "dom_group", None), INV, b"NULL problem"),
+    ("NULL traces", lambda g, p: setattr(g, "mid", None), INV, b"NULL trace"),
+]
+
+
+@pytest.mark.parametrize("name,breaks,status,msg", NOALLOC_CASES,
+                         ids=[c[0] for c in NOALLOC_CASES])
+def test_noalloc_entry_point_rejects_on_the_host(lib, name, breaks, status, msg):
+    g, p, _ = _valid()
+    if breaks is None:
+        st = lib.tt_semblance_eval_noalloc(None, None, FAKE, 1, FAKE, None)
+    else:
+        breaks(g, p)
+        st = lib.tt_semblance_eval_noalloc(ctypes.byref(g), ctypes.byref(p), FAKE, 4, FAKE,
+                                           None)
+    assert st == status, (name, st, lib.tt_last_error(None))
+    assert msg in lib.tt_last_error(None)
+
+
+def test_noalloc_with_no_domains_is_a_no_op(lib):
+    g, p, _ = _valid()
+    p.n_dom = 0
+    assert lib.tt_semblance_eval_noalloc(ctypes.byref(g), ctypes.byref(p), None, 4, None,
+                                         None) == _lib.TT_OK
