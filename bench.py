@@ -384,10 +384,10 @@ def main():
     import torch.distributed as dist
 
     world, rank, local = rank_env()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)  # before the process group: NCCL binds this rank's GPU
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
 
     from paper_2304_11399_gb300 import build as _build
     _build.build()
