@@ -208,6 +208,10 @@ tt_status tt_stack(tt_ctx* ctx, const float* theta, float* out, void* stream);
  * block); FP32 arithmetic with one rounding per operation, so results are
  * bit-reproducible. pop and fit [n_dom][NP] are updated in place;
  * best_idx [n_dom] may be NULL. */
+tt_status tt_de_step(tt_ctx* ctx, int32_t gen, float* pop, float* fit, const float* trial,
+                     const float* trial_fit, float* next_trial, int32_t* best_idx,
+                     void* stream);
+
 /* Copy the JADE adaptation state of a context created with cfg.adapt = 1
  * out to (save = 1) or in from (save = 0) caller arrays, for checkpointing an
  * adaptive search driven by tt_de_step: mu [n_dom][2] (mu_CR, mu_F), n_arc
@@ -220,16 +224,12 @@ tt_status tt_stack(tt_ctx* ctx, const float* theta, float* out, void* stream);
 tt_status tt_jade_state(tt_ctx* ctx, int32_t save, float* mu, int32_t* n_arc, float* archive,
                         float* F, float* CR, void* stream);
 
-tt_status tt_de_step(tt_ctx* ctx, int32_t gen, float* pop, float* fit, const float* trial,
-                     const float* trial_fit, float* next_trial, int32_t* best_idx,
-                     void* stream);
-
 /* best_theta [n_dom][D] and best_S [n_dom] (either may be NULL) = the
  * member with the highest fitness of each domain (lowest index on ties). */
 tt_status tt_best_snapshot(tt_ctx* ctx, const float* pop, const float* fit, float* best_theta,
                            float* best_S, void* stream);
 
-/* Neighbour exchange (Sec. 3.4 "Information propagation"): on the m0-major
+/* Neighbour exchange (Sec. 3.3 "Information propagation"): on the m0-major
  * grid n_m0 x n_t0 (n_m0 * n_t0 == n_dom), every domain imports the
  * snapshot best_theta [n_dom][D] of its present neighbours, in the order
  * (it0-1), (it0+1), (m0-1), (m0+1), into its worst members ranked by
@@ -247,7 +247,7 @@ tt_status tt_neighbor_exchange(tt_ctx* ctx, int32_t n_m0, int32_t n_t0, const fl
  * S [n_dom] receives its semblance. Uses the context's scratch. */
 tt_status tt_polish(tt_ctx* ctx, float* theta, float* S, int32_t steps, float lr, void* stream);
 
-/* Evolution by neighborhood similarity in sweep mode (Sec. 3.4-3.6): the
+/* Evolution by neighborhood similarity in sweep mode (Sec. 3.3-3.6): the
  * grid's traces (m0) are cut into buckets of n_bucket consecutive traces;
  * every bucket runs a forward exploration (NP_f x NG_f, seeded with the best
  * of the same sample on the previous trace) and n_cycle backward-and-forward
@@ -314,8 +314,10 @@ tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
  *                 0: launch eagerly. Searches run eagerly while profiling is
  *                 enabled.
  *  TT_OPT_SPLIT   1 (default): a forward evaluation of fewer than
- *                 TT_SPLIT_MAX_PAIRS (domain, vector) pairs -- too few to fill
- *                 the GPU at one warp per 64 pairs -- runs a kernel in which
+ *                 n_sm x 32 x 64 (domain, vector) pairs, n_sm the device's
+ *                 multiprocessor count (TT_OPT_SPLIT_MAX_PAIRS reads the
+ *                 figure) -- too few to fill the GPU at one warp per 64
+ *                 pairs -- runs a kernel in which
  *                 the S warps of a block (8, 16 or 32, more for smaller
  *                 launches) share 64 pairs, each warp summing a contiguous
  *                 slice of every pair's aperture, the partial sums added in
@@ -327,9 +329,19 @@ tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
  *                 sums through the context's scratch, so split evaluations on
  *                 one context must not overlap on the GPU (one stream, or
  *                 events between streams). 0: never split.
+ *  TT_OPT_SPLIT_MAX_PAIRS  (read only) the split threshold above, in pairs.
+ *  TT_OPT_SM_COUNT  (read only) multiprocessors of the context's device,
+ *                 queried at tt_ctx_create; the split thresholds and the
+ *                 persistent grid scale with it.
  *  Changing an option drops a captured graph. */
-enum { TT_OPT_KERNEL = 1, TT_OPT_BLOCK = 2, TT_OPT_SEARCH_GRAPH = 3, TT_OPT_SPLIT = 4 };
-#define TT_SPLIT_MAX_PAIRS (152 * 32 * 64)
+enum {
+  TT_OPT_KERNEL = 1,
+  TT_OPT_BLOCK = 2,
+  TT_OPT_SEARCH_GRAPH = 3,
+  TT_OPT_SPLIT = 4,
+  TT_OPT_SPLIT_MAX_PAIRS = 5,
+  TT_OPT_SM_COUNT = 6
+};
 enum { TT_KERNEL_PACKED = 1, TT_KERNEL_PERSISTENT = 2, TT_KERNEL_SCALAR = 3 };
 #define TT_N_TUNE_CANDIDATES 6
 tt_status tt_ctx_set_option(tt_ctx* ctx, int32_t option, int64_t value);
@@ -345,7 +357,7 @@ tt_status tt_ctx_get_option(const tt_ctx* ctx, int32_t option, int64_t* value);
 tt_status tt_ctx_autotune(tt_ctx* ctx, const float* theta, int32_t P, float* S,
                           float* times_ms, void* stream);
 
-/* The whole search (JADE loop of Sec. 2.1 with the exchange of Sec. 3.4):
+/* The whole search (JADE loop of Sec. 2.1 with the exchange of Sec. 3.3):
  * init, NG generations of select/mutate/evaluate, an exchange after every
  * exch_every-th selection, then cfg polish_steps of polishing. Writes
  * best_theta [n_dom][D] and best_S [n_dom] (device). *n_evals (host, may be
@@ -369,13 +381,17 @@ tt_status tt_search(tt_ctx* ctx, float* best_theta, float* best_S, uint64_t* n_e
  * TT_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
  * the library until the process exits; problems whose aperture lists hold
  * more than TT_NOALLOC_MAX_APERTURE_ENTRIES entries, and TT_OP_FOCRS problems,
- * are rejected with TT_ERR_UNSUPPORTED. The first call on a device (with that device current)
- * looks up the array's device address; make it before any stream capture.
- * Every call synchronises `stream` once, to read ap_ptr and the result of the
- * on-device validation (INVALID_ARG as for tt_ctx_create), then enqueues the
- * evaluation without waiting. All calls share the scratch array, which keeps
- * the last call's contents: calls that overlap on the GPU race on it, so
- * serialise them (one stream, or events). Error messages: tt_last_error(NULL). */
+ * are rejected with TT_ERR_UNSUPPORTED. Positions follow tt_semblance_eval's
+ * two forms (direct up to 2048 samples, the moveout form for longer
+ * records), so S agrees with the exact semblance to the same 1e-5. Every
+ * call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so a device reset by the
+ * host application between calls is harmless. Every call synchronises
+ * `stream` twice -- to read ap_ptr, then the result of the on-device
+ * validation (INVALID_ARG as for tt_ctx_create) -- and then enqueues the
+ * evaluation without waiting. All calls share the scratch array, which keeps the last call's contents: calls
+ * that overlap on the GPU race on it, so serialise them (one stream, or
+ * events). Error messages: tt_last_error(NULL). */
 #define TT_NOALLOC_SCRATCH_BYTES (4u << 20)
 #define TT_NOALLOC_MAX_APERTURE_ENTRIES 262128
 tt_status tt_semblance_eval_noalloc(const tt_gathers* gathers, const tt_problem* problem,

@@ -1,11 +1,11 @@
 """Neighbour exchange of best individuals (TEST INFRASTRUCTURE).
 
-Evolution by neighborhood similarity (Sec. 3.3 "Similarities between
-neighboring domains", Sec. 3.4 "Information propagation", Sec. 3.6): the
+Evolution by neighborhood similarity (Sec. 3.2 "Similarities between
+neighboring domains", Sec. 3.3 "Information propagation", Sec. 3.6): the
 best individual of a domain is introduced into the populations of the
 neighbouring zero-offset samples, i.e. the time samples above and below on
 the same trace and the same time sample on the adjacent traces (the four
-seeds of the backward step, Sec. 3.4), where it replaces a member.
+seeds of the backward step, Sec. 3.3), where it replaces a member.
 
 Readings taken here (the paper gives the sweep, not a synchronous rule):
 * Domains form an (m0, t0) grid laid out m0-major, d = im0 * n_t0 + it0.
@@ -16,7 +16,7 @@ Readings taken here (the paper gives the sweep, not a synchronous rule):
 * The q-th present neighbour's best replaces the q-th worst member, ranked
   by (semblance ascending, index ascending) over the members other than
   the domain's own best (argmax, lowest index on ties), so the domain's own
-  best is kept as the fourth seed of Sec. 3.4. Its semblance is then
+  best is kept as the fourth seed of Sec. 3.3. Its semblance is then
   evaluated at the receiving domain.
 """
 from __future__ import annotations

@@ -3,7 +3,7 @@
 Per domain (zero-offset sample) the JADE loop of Sec. 2.1 / Fig. 3 with
 p = 1, with fixed F, CR (``oracle.de``) or, when ``cfg.adapt`` is set, with
 JADE's adaptation of F and CR and its archive (``oracle.jade``), driven over
-all domains at once with the neighbour exchange of Sec. 3.4
+all domains at once with the neighbour exchange of Sec. 3.3
 (``oracle.exchange``):
 
     gen 0:          init population, evaluate it

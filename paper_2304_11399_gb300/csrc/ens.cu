@@ -1,5 +1,5 @@
 // Evolution by neighborhood similarity in sweep mode (tt_ens_search): the
-// paper's ENS (Sec. 3.4-3.6) on the m0-major (m0, t0) grid, cut into buckets
+// paper's ENS (Sec. 3.3-3.6) on the m0-major (m0, t0) grid, cut into buckets
 // of n_bucket consecutive traces (CMPs).
 //
 // Stages: a forward exploration (NP_f x NG_f, one seed: the best of the same

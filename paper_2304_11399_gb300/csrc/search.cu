@@ -1,5 +1,5 @@
 // Host driver of the whole search: the JADE loop of Sec. 2.1 (p = 1, fixed
-// F and CR) over every domain at once, the neighbour exchange of Sec. 3.4
+// F and CR) over every domain at once, the neighbour exchange of Sec. 3.3
 // after every exch_every-th selection, and the gradient polish. Everything
 // is enqueued on one stream; nothing synchronises. The selection of
 // generation g is fused into the step that mutates generation g+1 unless an

@@ -153,7 +153,7 @@ def test_exchange_result_is_the_best_of_own_and_neighbours_bests():
     """With the exchange as the last step (NG = exch_every, no polish), every
     sample's result is the best of its own pre-exchange best and the
     neighbours' pre-exchange bests evaluated at it: the imports replace
-    members other than the own best (Sec. 3.4). The pre-exchange bests are
+    members other than the own best (Sec. 3.3). The pre-exchange bests are
     those of the same search without exchange (same draws up to that point).
     Pins the snapshot (the bests, taken before any import), the cadence (after
     generation exch_every's selection) and the import count."""
