@@ -61,6 +61,7 @@ tt::EvalArgs tt_ctx::eval_args(const float* theta, int P, float* S) const {
   a.block = block;
   a.split = split ? 1 : 0;
   a.split_blocks = 1;
+  a.n_sm = n_sm;
   a.split_part = split_part;
   a.split_part_d = split_part_d;
   a.split_ticket = split_ticket;
@@ -98,6 +99,9 @@ extern "C" tt_status tt_ctx_set_option(tt_ctx* c, int32_t option, int64_t value)
     case TT_OPT_SPLIT:
       c->split = value != 0;
       break;
+    case TT_OPT_SPLIT_MAX_PAIRS:
+    case TT_OPT_SM_COUNT:
+      return tt_fail(c, TT_ERR_INVALID_ARG, "option %d is read only", option);
     default:
       return tt_fail(c, TT_ERR_INVALID_ARG, "unknown option %d", option);
   }
@@ -112,6 +116,8 @@ extern "C" tt_status tt_ctx_get_option(const tt_ctx* c, int32_t option, int64_t*
     case TT_OPT_BLOCK: *value = c->block; return TT_OK;
     case TT_OPT_SEARCH_GRAPH: *value = c->use_graph ? 1 : 0; return TT_OK;
     case TT_OPT_SPLIT: *value = c->split ? 1 : 0; return TT_OK;
+    case TT_OPT_SPLIT_MAX_PAIRS: *value = (int64_t)c->n_sm * tt::kSplitUnitsPerSm * 64; return TT_OK;
+    case TT_OPT_SM_COUNT: *value = c->n_sm; return TT_OK;
   }
   return tt_fail(nullptr, TT_ERR_INVALID_ARG, "unknown option %d", option);
 }
@@ -300,10 +306,13 @@ __global__ void k_inv(int n, const float* x, float* y) {
   if (i < n) y[i] = 1.0f / x[i];
 }
 
-int grid_for(long long n, int block = 256) {
+// blocks of a grid-stride loop over n items: enough to cover them, at most
+// 32 blocks per SM of the context's device
+int grid_for(const tt_ctx* c, long long n, int block = 256) {
   long long b = (n + block - 1) / block;
+  const long long cap = 32ll * c->n_sm;
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
-  if (b > 152 * 32) b = 152 * 32;
   return int(b);
 }
 
@@ -359,7 +368,7 @@ tt_status fill_traces(tt_ctx* c, const float* src, bool host, cudaStream_t s) {
       if (e != cudaSuccess) return tt_cuda_check(c, e, "stage traces");
       from = c->stage;
     }
-    k_pad_rows<__nv_bfloat16><<<grid_for(rows * c->pitch), 256, 0, s>>>(from, dst, r0, rows,
+    k_pad_rows<__nv_bfloat16><<<grid_for(c, rows * c->pitch), 256, 0, s>>>(from, dst, r0, rows,
                                                                         c->ns, c->pitch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tt_cuda_check(c, e, "convert traces");
@@ -417,7 +426,16 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tt_ctx* c = new tt_ctx();
-  cudaGetDevice(&c->device);
+  {
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess || c->n_sm < 1) {
+      free_ctx(c);
+      return tt_cuda_check(nullptr, e != cudaSuccess ? e : cudaErrorInvalidDevice,
+                           "query the device's multiprocessor count");
+    }
+  }
   c->n_traces = ga->n_traces;
   c->ns = ga->ns;
   c->storage = ga->storage;
@@ -459,7 +477,7 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
   TRY(dalloc(&c->d_err, 1), "alloc flag");
   TRY(cudaMemsetAsync(c->d_err, 0, 4, s), "clear flag");
   if (pr->n_groups > 0 || pr->n_dom > 0) {
-    k_validate<<<grid_for(std::max<long long>({(long long)pr->n_groups, c->nnz,
+    k_validate<<<grid_for(c, std::max<long long>({(long long)pr->n_groups, c->nnz,
                                                (long long)pr->n_dom})),
                  256, 0, s>>>(ga->n_traces, pr->n_groups, pr->n_dom, pr->group_dt,
                               pr->group_m0, pr->op == TT_OP_FOCRS ? pr->group_h0 : nullptr,
@@ -468,7 +486,7 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
     TRY(cudaGetLastError(), "validate");
   }
   if (ga->n_traces > 0 && ga->ns > 0) {
-    k_check_geom<<<grid_for(ga->n_traces), 256, 0, s>>>(ga->n_traces, ga->mid, ga->off,
+    k_check_geom<<<grid_for(c, ga->n_traces), 256, 0, s>>>(ga->n_traces, ga->mid, ga->off,
                                                         c->d_err);
     TRY(cudaGetLastError(), "validate geometry");
   }
@@ -570,17 +588,17 @@ extern "C" tt_status tt_ctx_create(tt_ctx** out, const tt_gathers* ga, const tt_
     }
   }
   TRY(dalloc(&c->queue, 1), "alloc queue");
-  TRY(dalloc(&c->split_part, size_t(tt::kSplitPartSets) * 64 * tt::kSplitPartStride),
+  TRY(dalloc(&c->split_part, size_t(tt::split_part_sets(c->n_sm)) * 64 * tt::kSplitPartStride),
       "alloc split scratch");
-  TRY(dalloc(&c->split_part_d, size_t(tt::kSplitPartSets) * 64), "alloc split scratch");
-  TRY(dalloc(&c->split_ticket, size_t(tt::kSplitMultiUnits)), "alloc split tickets");
-  TRY(cudaMemsetAsync(c->split_ticket, 0, size_t(tt::kSplitMultiUnits) * sizeof(unsigned), s),
+  TRY(dalloc(&c->split_part_d, size_t(tt::split_part_sets(c->n_sm)) * 64), "alloc split scratch");
+  TRY(dalloc(&c->split_ticket, size_t(tt::split_tickets(c->n_sm))), "alloc split tickets");
+  TRY(cudaMemsetAsync(c->split_ticket, 0, size_t(tt::split_tickets(c->n_sm)) * sizeof(unsigned), s),
       "clear split tickets");
-  TRY(dalloc(&c->split_part2, size_t(tt::kSplitPartSets) * 64 * tt::kSplitPartStride),
+  TRY(dalloc(&c->split_part2, size_t(tt::split_part_sets(c->n_sm)) * 64 * tt::kSplitPartStride),
       "alloc split scratch");
-  TRY(dalloc(&c->split_part_d2, size_t(tt::kSplitPartSets) * 64), "alloc split scratch");
-  TRY(dalloc(&c->split_ticket2, size_t(tt::kSplitMultiUnits)), "alloc split tickets");
-  TRY(cudaMemsetAsync(c->split_ticket2, 0, size_t(tt::kSplitMultiUnits) * sizeof(unsigned), s),
+  TRY(dalloc(&c->split_part_d2, size_t(tt::split_part_sets(c->n_sm)) * 64), "alloc split scratch");
+  TRY(dalloc(&c->split_ticket2, size_t(tt::split_tickets(c->n_sm))), "alloc split tickets");
+  TRY(cudaMemsetAsync(c->split_ticket2, 0, size_t(tt::split_tickets(c->n_sm)) * sizeof(unsigned), s),
       "clear split tickets");
   {
     size_t nd = size_t(c->n_dom), Dz = size_t(D);

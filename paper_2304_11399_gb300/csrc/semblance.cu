@@ -16,7 +16,6 @@ extern template SFn pick_stack<TT_OP_FOCRS>(int, bool);
 namespace {
 
 using sk::KFn;
-using sk::kSplitMaxUnits;
 
 constexpr int kDirectMax = 2048;  // direct position up to u = 2048 samples
 
@@ -41,19 +40,19 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
   if (grad) {
     fn = pick(sk::kKindGrad, a, mv);
     blocks = (n + block - 1) / block;
-  } else if (a.split && (n + 63) / 64 < kSplitMaxUnits) {
+  } else if (a.split && (n + 63) / 64 < (long long)a.n_sm * kSplitUnitsPerSm) {
     // too few units to fill the GPU: each unit's aperture split over the
     // warps of B blocks, (S, B) by launch size only
     fn = pick(sk::kKindSplit, a, mv);
     if (!fn) return cudaErrorInvalidValue;
     const long long units = (n + 63) / 64;
-    int S = sk::split_warps(units);
+    int S = sk::split_warps(units, a.n_sm);
     b.split_blocks = 1;
     if (a.split_part && a.split_ticket) {
-      if (units <= kSplitSmallUnits) {
+      if (units <= (long long)a.n_sm * kSplitSmallPerSm) {
         S = sk::kSplitMultiWarps;
         b.split_blocks = kSplitMaxBlocks;
-      } else if (units < kSplitMultiUnits) {
+      } else if (units < (long long)a.n_sm * kSplitMultiPerSm) {
         S = 8;
         b.split_blocks = 2;
       }
@@ -72,12 +71,10 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
     const long long units = (n + 63) / 64;
     blocks = (units + block / 32 - 1) / (block / 32);
     if (a.kernel == TT_KERNEL_PERSISTENT && a.queue) {
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaError_t e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0);
+      int per_sm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0);
       if (e != cudaSuccess) return e;
-      const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
+      const long long resident = (long long)a.n_sm * (per_sm > 0 ? per_sm : 1);
       if (resident < blocks) blocks = resident;
       e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
       if (e != cudaSuccess) return e;

@@ -398,25 +398,26 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
 // shared memory and are added in slice order; with B > 1 each block writes
 // its sums to global scratch and the last block of the unit to arrive (an
 // atomic ticket, no waiting) adds the B block sums in block order. (S, B)
-// is (16, 4) up to 304 units, (8, 2) below 1824 and (8, 1) above, so that
+// is (16, 4) up to 2 units per SM, (8, 2) below 12 per SM and (8, 1) above
+// (304 and 1824 units on a 152-SM device), so that
 // the GPU stays busy. The summation order depends on (S, B) and
 // differs from the one-warp-per-unit kernel, so all are chosen by launch
 // size alone -- every variant of a launch runs the same code -- and results
 // stay reproducible.
 constexpr int kSplitMaxWarps = 16;
-static_assert(TT_SPLIT_MAX_PAIRS % 64 == 0, "split threshold is counted in 64-pair units");
-constexpr long long kSplitMaxUnits = TT_SPLIT_MAX_PAIRS / 64;
 
-// warps per block of a one-block-per-unit split launch of `units` units:
-// 8 once that keeps about 152 x 32 warps resident, else 16
-inline int split_warps(long long units) { return units * 8 >= 152ll * 32 ? 8 : kSplitMaxWarps; }
+// warps per block of a one-block-per-unit split launch of `units` units on a
+// device of n_sm SMs: 8 once that keeps about 32 warps resident per SM, else 16
+inline int split_warps(long long units, int n_sm) {
+  return units * 8 >= (long long)n_sm * 32 ? 8 : kSplitMaxWarps;
+}
 
-// Launches of at most kSplitSmallUnits units run kSplitMultiWarps warps per
+// Launches of at most n_sm * kSplitSmallPerSm units run kSplitMultiWarps warps per
 // block and kSplitMaxBlocks blocks per unit: 64 slices per aperture in
 // 512-thread blocks, two of which share an SM, so one block's barrier overlaps
 // the other's loads. The best of the (S, B) pairs timed on ENS sweeps
 // (S x B = 64 with 512- or 256-thread blocks; 1024-thread blocks were 12-20%
-// slower). Below kSplitMultiUnits units, (8, 2): timed 17% faster than
+// slower). Below n_sm * kSplitMultiPerSm units, (8, 2): timed 17% faster than
 // (8, 1) on the 938-unit launches of an ENS 30 x 30 sweep, while from about
 // 2500 units (ENS 80 x 80) one block per unit is best.
 constexpr int kSplitMultiWarps = 16;

@@ -15,15 +15,24 @@ namespace tt {
 // parameters per operator: CMP (C), CRS (A, B, C), FO-CRS (Am, Ah, Bmm, Bmh, Bhh)
 constexpr int op_dim(int op) { return op == TT_OP_CMP ? 1 : op == TT_OP_CRS ? 3 : 5; }
 
-// Split launches of fewer than kSplitMultiUnits units spread a unit over
-// several blocks (4 up to kSplitSmallUnits units, else 2); their partial
-// sums need this scratch.
-constexpr int kSplitSmallUnits = 304;
-constexpr int kSplitMultiUnits = 1824;
+// Small-launch split thresholds, in 64-pair units per SM of the device
+// (the SM count is queried when a context is created): a forward launch of
+// fewer than n_sm * kSplitUnitsPerSm units (one warp per unit then leaves
+// SMs short of their 32 resident warps) splits each unit's aperture over
+// the warps of a block; up to n_sm * kSplitSmallPerSm units a unit spreads
+// over kSplitMaxBlocks blocks, below n_sm * kSplitMultiPerSm over two. The
+// multi-block launches combine partial sums in context scratch.
+constexpr int kSplitUnitsPerSm = 32;
+constexpr int kSplitSmallPerSm = 2;
+constexpr int kSplitMultiPerSm = 12;
 constexpr int kSplitMaxBlocks = 4;
-constexpr int kSplitPartSets = kSplitMultiUnits * 2 > kSplitSmallUnits * kSplitMaxBlocks
-                                   ? kSplitMultiUnits * 2
-                                   : kSplitSmallUnits * kSplitMaxBlocks;
+// scratch sets (one per block of a multi-block split launch) and tickets
+// (one per unit) for a device of n_sm SMs
+inline long long split_part_sets(int n_sm) {
+  const long long a = 2ll * kSplitMultiPerSm, b = (long long)kSplitSmallPerSm * kSplitMaxBlocks;
+  return (a > b ? a : b) * n_sm;
+}
+inline long long split_tickets(int n_sm) { return (long long)kSplitMultiPerSm * n_sm; }
 constexpr int kSplitPartStride = 2 * 8 + 2;  // floats per pair: K + 1 for the widest window
 
 // Padded trace layout: sample n of trace r lives at r * pitch + kPadFront + n.
@@ -55,9 +64,10 @@ struct EvalArgs {
   int block;                // threads per block: 128 or 256
   int split;                // 1: small forward launches split the aperture over warps
   int split_blocks;         // blocks per unit of a split launch (set by the launcher)
-  float* split_part;        // [kSplitPartSets][64][K + 1] block partial sums (s_k, E)
-  double* split_part_d;     // [kSplitPartSets][64] block partial FP64 energies
-  unsigned* split_ticket;   // [kSplitMultiUnits] arrivals per unit, zero between launches
+  int n_sm;                 // SMs of the device (split thresholds, persistent grid)
+  float* split_part;        // [split_part_sets][64][K + 1] block partial sums (s_k, E)
+  double* split_part_d;     // [split_part_sets][64] block partial FP64 energies
+  unsigned* split_ticket;   // [split_tickets] arrivals per unit, zero between launches
   unsigned long long* queue;  // persistent mode: work-unit counter, zero at launch
 };
 
@@ -167,6 +177,7 @@ cudaError_t launch_polish_update(int n_dom, int D, float* th, const float* g, co
 
 struct tt_ctx {
   int device = 0;
+  int n_sm = 1;             // multiprocessors of the device (queried at creation)
   // gathers (padded device copy)
   int n_traces = 0, ns = 0, storage = TT_STORE_F32, pitch = 0;
   void* traces = nullptr;
@@ -195,7 +206,7 @@ struct tt_ctx {
         *pol_bS = nullptr;
   int* d_err = nullptr;     // device-side validation flag
   unsigned long long* queue = nullptr;  // persistent-kernel work counter
-  float* split_part = nullptr;          // multi-block split scratch (tt::kSplitPartSets sets)
+  float* split_part = nullptr;          // multi-block split scratch (tt::split_part_sets sets)
   double* split_part_d = nullptr;
   unsigned* split_ticket = nullptr;
   // a second split scratch and a side stream: the ENS sweep evaluates each

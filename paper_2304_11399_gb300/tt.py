@@ -286,7 +286,7 @@ _KERNELS = {"packed": L.TT_KERNEL_PACKED, "persistent": L.TT_KERNEL_PERSISTENT,
 def tt_ctx_set_option(ctx: Context, option: str, value):
     """option: "kernel" ("packed" | "persistent" | "scalar"), "block" (128 | 256),
     "search_graph" (bool) or "split" (bool: split the aperture over the warps
-    of a block for launches of fewer than TT_SPLIT_MAX_PAIRS pairs)."""
+    of a block for launches of fewer than the "split_max_pairs" threshold)."""
     if option == "kernel":
         code, v = L.TT_OPT_KERNEL, _KERNELS[value]
     elif option == "block":
@@ -301,8 +301,11 @@ def tt_ctx_set_option(ctx: Context, option: str, value):
 
 
 def tt_ctx_get_option(ctx: Context, option: str):
+    """option: as for tt_ctx_set_option, or the read-only "split_max_pairs"
+    (split threshold in pairs) and "sm_count" (the device's multiprocessors)."""
     code = {"kernel": L.TT_OPT_KERNEL, "block": L.TT_OPT_BLOCK,
-            "search_graph": L.TT_OPT_SEARCH_GRAPH, "split": L.TT_OPT_SPLIT}[option]
+            "search_graph": L.TT_OPT_SEARCH_GRAPH, "split": L.TT_OPT_SPLIT,
+            "split_max_pairs": L.TT_OPT_SPLIT_MAX_PAIRS, "sm_count": L.TT_OPT_SM_COUNT}[option]
     v = C.c_int64()
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_get_option(ctx.handle, code, C.byref(v)))
     if option == "kernel":

@@ -36,7 +36,7 @@ def _all_variants(ctx, theta):
     tt.tt_ctx_set_option(ctx, "kernel", "packed")
     tt.tt_ctx_set_option(ctx, "block", 256)
     n_pairs = split[0].size
-    if n_pairs < _lib.TT_SPLIT_MAX_PAIRS:
+    if n_pairs < tt.tt_ctx_get_option(ctx, "split_max_pairs"):
         for v in split[1:]:
             assert np.array_equal(v, split[0])
     else:  # too many pairs to split: the option changes nothing
