@@ -11,15 +11,15 @@
 // -- lives in the file-scope device array below: TT_NOALLOC_SCRATCH_BYTES
 // (4 MiB) that every GPU which loads the library holds until the process
 // exits. Host code may not use the array's name as a device address (in host
-// code it names a host-side stand-in), so the first call on each device, with
-// that device current, asks the runtime for the array's device address with
-// cudaGetSymbolAddress and every later call on that device reuses it; make
-// that first call before any stream capture. All calls share the array and
-// it keeps the last call's contents: the flag is cleared by every call, the
-// table is rewritten, and calls that overlap on the GPU (different streams
-// or threads) race on it.
+// code it names a host-side stand-in), so every call asks the runtime for the
+// array's device address on the current device with cudaGetSymbolAddress
+// (a lookup, no allocation); looking it up each time keeps a call correct
+// after the host application has reset the device. All calls share the array
+// and it keeps the last call's contents: the flag is cleared by every call,
+// the table is rewritten, and calls that overlap on the GPU (different
+// streams or threads) race on it. Every call synchronises its stream twice:
+// to read ap_ptr, then the validation flag.
 #include <algorithm>
-#include <mutex>
 
 #include "tt_internal.cuh"
 
@@ -33,25 +33,18 @@ static_assert(kHeaderBytes + size_t(kMaxEntries) * sizeof(float4) <= kScratchByt
 
 static __device__ __align__(256) unsigned char tt_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set up once).
-tt_status scratch_address(unsigned char** out) {
+// Device address of the scratch array on the current device, and that
+// device's multiprocessor count (for grid-stride launches).
+tt_status scratch_address(unsigned char** out, int* n_sm) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return tt_cuda_check(nullptr, e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices)
-    return tt_fail(nullptr, TT_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, tt_noalloc_scratch);
-    if (e != cudaSuccess) return tt_cuda_check(nullptr, e, "cudaGetSymbolAddress(scratch)");
-    g_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_addr[dev]);
+  e = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return tt_cuda_check(nullptr, e, "multiprocessor count");
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, tt_noalloc_scratch);
+  if (e != cudaSuccess) return tt_cuda_check(nullptr, e, "cudaGetSymbolAddress(scratch)");
+  *out = static_cast<unsigned char*>(p);
   return TT_OK;
 }
 
@@ -81,97 +74,140 @@ __global__ void k_na_validate(int n_traces, int G, int n_dom, const float* g_dt,
   }
 }
 
-// One warp per group: entry e -> (dm, dm^2, h^2, trace index).
+// One warp per group (grid-stride over groups): entry e -> (dm, dm^2, h^2,
+// trace index).
 __global__ void k_na_table(int G, const int* ap_ptr, const int* ap_idx, const float* g_m0,
                            const float* mid, const float* off, float4* tab) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= G) return;
-  const float m0 = g_m0[warp];
-  for (int e = ap_ptr[warp] + lane; e < ap_ptr[warp + 1]; e += 32) {
-    const int r = ap_idx[e];
-    const float dm = mid[r] - m0, h = off[r];
-    tab[e] = make_float4(dm, dm * dm, h * h, __int_as_float(r));
+  for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G;
+       g += warps) {
+    const float m0 = g_m0[g];
+    for (int e = ap_ptr[g] + lane; e < ap_ptr[g + 1]; e += 32) {
+      const int r = ap_idx[e];
+      const float dm = mid[r] - m0, h = off[r];
+      tab[e] = make_float4(dm, dm * dm, h * h, __int_as_float(r));
+    }
   }
 }
 
-// One (domain, individual) pair per thread, samples read from the caller's
-// [n_traces][ns] traces with the record's zero extension done by bounds
-// checks (no padded copy).
-template <int OP, int W>
+// One (domain, individual) pair per thread (grid-stride over pairs), samples
+// read from the caller's [n_traces][ns] traces with the record's zero
+// extension done by bounds checks (no padded copy). The window centre
+// u = t / dt (samples) is found directly, u = sqrt(U), for records of up to
+// 2048 samples (MV false); longer records (MV true) take u = it0 + du, with
+// the moveout du the root of du^2 + 2 it0 du - V = 0, V = U - it0^2 formed
+// from its small terms, from one reciprocal-square-root estimate and one
+// Newton step: it0 is an exact integer and du is small, so the interpolation
+// weight keeps ~1e-5-sample accuracy where u itself (thousands of samples)
+// would round at ~1e-4 samples. U < 0 (no real traveltime) gives NaN, which
+// the clamp to ns + w maps to a window of zeros.
+template <int OP, int W, bool MV>
 __global__ void __launch_bounds__(256)
     k_na_semblance(const float* __restrict__ traces, int ns, const float4* __restrict__ tab,
                    const int* ap_ptr, const float* g_dt, const int* dom_it0,
                    const int* dom_group, int n_dom, int P, const float* theta, float* S) {
   constexpr int K = 2 * W + 1;
   constexpr int D = OP == TT_OP_CMP ? 1 : 3;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (long long)n_dom * P) return;
-  const int d = int(q / P);
-  const int g = dom_group[d];
-  const float inv_dt = 1.0f / g_dt[g];
-  const float p0 = float(dom_it0[d]);
-  const float* th = theta + q * D;
-  const float ca = OP == TT_OP_CMP ? 0.f : th[0] * inv_dt;
-  const float cb = OP == TT_OP_CMP ? 0.f : th[1] * inv_dt * inv_dt;
-  const float cc = th[D - 1] * inv_dt * inv_dt;
-  const float umax = float(ns + W);
-  float s[K];
+  const long long n = (long long)n_dom * P;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+    const int d = int(q / P);
+    const int g = dom_group[d];
+    const float inv_dt = 1.0f / g_dt[g];
+    const int it0 = dom_it0[d];
+    const float p0 = float(it0);
+    const float* th = theta + q * D;
+    const float ca = OP == TT_OP_CMP ? 0.f : th[0] * inv_dt;
+    const float cb = OP == TT_OP_CMP ? 0.f : th[1] * inv_dt * inv_dt;
+    const float cc = th[D - 1] * inv_dt * inv_dt;
+    const float umax = float(ns + W);
+    float s[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) s[k] = 0.f;
-  float E = 0.f;
-  const int e0 = ap_ptr[g], e1 = ap_ptr[g + 1];
-  for (int e = e0; e < e1; ++e) {
-    const float4 t4 = tab[e];
-    const float qv = fmaf(ca, t4.x, p0);
-    const float U = fmaf(cb, t4.y, fmaf(cc, t4.z, qv * qv));
-    const float u = fminf(sqrtf(U), umax);  // NaN (U < 0) -> umax: all-zero window
-    const float fl = truncf(u);
-    const float f = u - fl;
-    const int j0 = int(fl) - W;
-    const float* row = traces + (size_t)__float_as_int(t4.w) * ns;
-    float xv[K + 1];
+    for (int k = 0; k < K; ++k) s[k] = 0.f;
+    float E = 0.f;
+    const int e0 = ap_ptr[g], e1 = ap_ptr[g + 1];
+    for (int e = e0; e < e1; ++e) {
+      const float4 t4 = tab[e];
+      float f;
+      int j;
+      if (!MV) {
+        const float qv = fmaf(ca, t4.x, p0);
+        const float U = fmaf(cb, t4.y, fmaf(cc, t4.z, qv * qv));
+        const float u = fminf(sqrtf(U), umax);
+        const float fl = truncf(u);
+        f = u - fl;
+        j = int(fl);
+      } else {
+        const float x = ca * t4.x;
+        const float V = fmaf(x, x + 2.f * p0, fmaf(cb, t4.y, cc * t4.z));
+        const float U = fmaf(p0, p0, 1e-30f) + V;  // the bias keeps U = 0 finite
+        const float r = rsqrtf(U);
+        const float du0 = fmaf(U, r, -p0);
+        float du = fmaf(-0.5f * r, fmaf(du0, du0 + 2.f * p0, -V), du0);
+        du = fmaxf(fminf(du, umax - p0), -p0);
+        const float fl = floorf(du);
+        f = du - fl;
+        j = it0 + int(fl);
+      }
+      const int j0 = j - W;
+      const float* row = traces + (size_t)__float_as_int(t4.w) * ns;
+      float xv[K + 1];
 #pragma unroll
-    for (int k = 0; k <= K; ++k) {
-      const int n = j0 + k;
-      xv[k] = (n >= 0 && n < ns) ? __ldg(row + n) : 0.f;
+      for (int k = 0; k <= K; ++k) {
+        const int m = j0 + k;
+        xv[k] = (m >= 0 && m < ns) ? __ldg(row + m) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float ak = fmaf(f, xv[k + 1] - xv[k], xv[k]);
+        s[k] += ak;
+        E = fmaf(ak, ak, E);
+      }
     }
+    float Q = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float ak = fmaf(f, xv[k + 1] - xv[k], xv[k]);
-      s[k] += ak;
-      E = fmaf(ak, ak, E);
-    }
+    for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
+    const float N = float(e1 - e0);
+    S[q] = (E > 0.f) ? Q / (N * E) : 0.f;
   }
-  float Q = 0.f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) Q = fmaf(s[k], s[k], Q);
-  const float N = float(e1 - e0);
-  S[q] = (E > 0.f) ? Q / (N * E) : 0.f;
 }
 
 using NaFn = void (*)(const float*, int, const float4*, const int*, const float*, const int*,
                       const int*, int, int, const float*, float*);
 
-template <int OP>
-NaFn pick(int W) {
+template <int OP, bool MV>
+NaFn pick_w(int W) {
   switch (W) {
-    case 0: return k_na_semblance<OP, 0>;
-    case 1: return k_na_semblance<OP, 1>;
-    case 2: return k_na_semblance<OP, 2>;
-    case 3: return k_na_semblance<OP, 3>;
-    case 4: return k_na_semblance<OP, 4>;
-    case 5: return k_na_semblance<OP, 5>;
-    case 6: return k_na_semblance<OP, 6>;
-    case 7: return k_na_semblance<OP, 7>;
-    case 8: return k_na_semblance<OP, 8>;
+    case 0: return k_na_semblance<OP, 0, MV>;
+    case 1: return k_na_semblance<OP, 1, MV>;
+    case 2: return k_na_semblance<OP, 2, MV>;
+    case 3: return k_na_semblance<OP, 3, MV>;
+    case 4: return k_na_semblance<OP, 4, MV>;
+    case 5: return k_na_semblance<OP, 5, MV>;
+    case 6: return k_na_semblance<OP, 6, MV>;
+    case 7: return k_na_semblance<OP, 7, MV>;
+    case 8: return k_na_semblance<OP, 8, MV>;
   }
   return nullptr;
 }
 
-int grid_for(long long n) {
-  long long b = (n + 255) / 256;
-  return int(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+// positions by the moveout form for records longer than this many samples
+constexpr int kDirectMax = 2048;
+
+NaFn pick(int op, int W, bool mv) {
+  if (op == TT_OP_CMP) return mv ? pick_w<TT_OP_CMP, true>(W) : pick_w<TT_OP_CMP, false>(W);
+  return mv ? pick_w<TT_OP_CRS, true>(W) : pick_w<TT_OP_CRS, false>(W);
+}
+
+// blocks of a grid-stride launch over n items, threads_per_item threads each:
+// enough to cover them, at most 32 blocks of 256 threads per SM
+unsigned grid_for(long long n, int n_sm, int threads_per_item = 1) {
+  long long b = (n * threads_per_item + 255) / 256;
+  const long long cap = 32ll * (n_sm > 0 ? n_sm : 1);
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return unsigned(b);
 }
 
 }  // namespace
@@ -202,7 +238,8 @@ extern "C" tt_status tt_semblance_eval_noalloc(const tt_gathers* ga, const tt_pr
     return tt_fail(nullptr, TT_ERR_INVALID_ARG, "NULL trace/geometry pointer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned char* scratch = nullptr;
-  tt_status st = scratch_address(&scratch);
+  int n_sm = 1;
+  tt_status st = scratch_address(&scratch, &n_sm);
   if (st != TT_OK) return st;
   int* flag = reinterpret_cast<int*>(scratch);
   float4* tab = reinterpret_cast<float4*>(scratch + kHeaderBytes);
@@ -224,7 +261,8 @@ extern "C" tt_status tt_semblance_eval_noalloc(const tt_gathers* ga, const tt_pr
   e = cudaMemsetAsync(flag, 0, sizeof(int), s);
   if (e != cudaSuccess) return tt_cuda_check(nullptr, e, "clear flag");
   k_na_validate<<<grid_for(std::max<long long>((long long)pr->n_groups,
-                                              std::max<long long>(nnz, pr->n_dom))),
+                                              std::max<long long>(nnz, pr->n_dom)),
+                           n_sm),
                   256, 0, s>>>(ga->n_traces, pr->n_groups, pr->n_dom, pr->group_dt,
                                pr->group_m0, pr->ap_ptr, pr->ap_idx, nnz, pr->dom_it0,
                                pr->dom_group, ga->mid, ga->off, flag);
@@ -241,16 +279,14 @@ extern "C" tt_status tt_semblance_eval_noalloc(const tt_gathers* ga, const tt_pr
                                 "dom_it0 must be in [0, 2^24)"};
     return tt_fail(nullptr, TT_ERR_INVALID_ARG, "%s", msg[herr]);
   }
-  k_na_table<<<(pr->n_groups * 32 + 255) / 256, 256, 0, s>>>(
+  k_na_table<<<grid_for(pr->n_groups, n_sm, 32), 256, 0, s>>>(
       pr->n_groups, pr->ap_ptr, pr->ap_idx, pr->group_m0, ga->mid, ga->off, tab);
   e = cudaGetLastError();
   if (e != cudaSuccess) return tt_cuda_check(nullptr, e, "aperture table");
-  NaFn fn = pr->op == TT_OP_CMP ? pick<TT_OP_CMP>(pr->half_window)
-                                : pick<TT_OP_CRS>(pr->half_window);
+  NaFn fn = pick(pr->op, pr->half_window, ga->ns + pr->half_window > kDirectMax);
   const long long n = (long long)pr->n_dom * P;
-  fn<<<unsigned((n + 255) / 256), 256, 0, s>>>(ga->traces, ga->ns, tab, pr->ap_ptr,
-                                                pr->group_dt, pr->dom_it0, pr->dom_group,
-                                                pr->n_dom, P, theta, S);
+  fn<<<grid_for(n, n_sm), 256, 0, s>>>(ga->traces, ga->ns, tab, pr->ap_ptr, pr->group_dt,
+                                       pr->dom_it0, pr->dom_group, pr->n_dom, P, theta, S);
   e = cudaGetLastError();
   if (e != cudaSuccess) return tt_cuda_check(nullptr, e, "allocation-free semblance");
   return TT_OK;

@@ -110,3 +110,72 @@ def test_noalloc_rejects_oversize_and_invalid_input():
     S = torch.zeros((prob.n_dom, 2), device=dev())
     assert _noalloc(lib, g, p, th, S) == _lib.TT_ERR_INVALID_ARG
     assert b"ap_idx" in lib.tt_last_error(None)
+
+
+def test_noalloc_long_record_matches_oracle():
+    """3000-sample records at 2 ms: window centres near u = 3000 samples,
+    where FP32 rounding of u itself would move S by ~2e-5. The entry point
+    takes the moveout form of the position there and stays within 1e-5 of
+    the FP64 oracle, and of the context path, on two calls in a row."""
+    import oracle
+    lib = _lib.load()
+    wl = configs.large_line(31, n_cmp=5, ns=3000, n_events=12, ap_half=2, cmps=[2],
+                            t0_range=(2300, 3000))
+    prob = wl.problem
+    rng = np.random.default_rng(4)
+    theta = random_theta(prob.n_dom, 4, wl.de.lo, wl.de.hi, 5)
+    # and the generating parameters of the events, recentred to the CMP, at
+    # their own zero-offset samples (semblance near 1 there)
+    for ev in wl.line.events:
+        t = synth.crs_recentre(ev, wl.line.cmp_x[2])
+        if t is None:
+            continue
+        it = int(round(t[0] / wl.dt))
+        if 2300 <= it < 3000:
+            theta[it - 2300, rng.integers(4)] = t[1:4]
+    g, p, keep = _cabi_args(wl.traces, wl.mid, wl.off, prob)
+    th = to_dev(theta)
+    S1 = torch.full((prob.n_dom, 4), -1.0, device=dev())
+    S2 = torch.full((prob.n_dom, 4), -1.0, device=dev())
+    assert _noalloc(lib, g, p, th, S1) == _lib.TT_OK, lib.tt_last_error(None)
+    assert _noalloc(lib, g, p, th, S2) == _lib.TT_OK, lib.tt_last_error(None)
+    torch.cuda.synchronize()
+    S1, S2 = S1.cpu().numpy(), S2.cpu().numpy()
+    assert np.array_equal(S1, S2)
+    ref = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, prob, theta)
+    assert ref.max() > 0.2  # the events are found: not only noise is compared
+    assert np.max(np.abs(S1 - ref)) <= TOL
+    assert np.max(np.abs(S1 - _context_eval(wl.traces, wl.mid, wl.off, prob, theta))) <= TOL
+
+
+@pytest.mark.parametrize("case,needle", [
+    ("ap_ptr", b"non-decreasing"), ("dt", b"dt"), ("dom_group", b"dom_group"),
+    ("dom_it0", b"dom_it0")])
+def test_noalloc_device_validation_flags(case, needle):
+    """Each input error that only the device-side validation sees is
+    reported as TT_ERR_INVALID_ARG with its own message, before the table
+    is built or any sample is read: a decreasing ap_ptr (the check that
+    keeps the table's writes inside the fixed scratch array), a zero dt, a
+    domain's group equal to n_groups and an it0 of 2^24."""
+    lib = _lib.load()
+    wl = small_line(23, n_cmp=4, ns=80, ap_half=1)
+    bad = synth.Problem(**{**wl.problem.__dict__})
+    if case == "ap_ptr":
+        bad.ap_ptr = wl.problem.ap_ptr.copy()
+        bad.ap_ptr[1] = bad.ap_ptr[2] + 1  # ends still 0 and nnz
+    elif case == "dt":
+        bad.group_dt = wl.problem.group_dt.copy()
+        bad.group_dt[1] = 0.0
+    elif case == "dom_group":
+        bad.dom_group = wl.problem.dom_group.copy()
+        bad.dom_group[7] = bad.group_m0.size
+    else:
+        bad.dom_it0 = wl.problem.dom_it0.copy()
+        bad.dom_it0[3] = 1 << 24
+    g, p, keep = _cabi_args(wl.traces, wl.mid, wl.off, bad)
+    th = to_dev(random_theta(bad.n_dom, 2, wl.de.lo, wl.de.hi, 6))
+    S = torch.full((bad.n_dom, 2), -1.0, device=dev())
+    assert _noalloc(lib, g, p, th, S) == _lib.TT_ERR_INVALID_ARG
+    assert needle in lib.tt_last_error(None)
+    torch.cuda.synchronize()
+    assert torch.all(S == -1.0)  # nothing written
