@@ -1,6 +1,6 @@
 """Evolution by neighborhood similarity, sweep mode (TEST INFRASTRUCTURE).
 
-The paper's ENS (Sec. 3.4 "Information propagation", Sec. 3.5 "The
+The paper's ENS (Sec. 3.3 "Information propagation", Sec. 3.5 "The
 performance-quality trade-off by an interpolation process", Sec. 3.6
 "Evolution by neighborhood similarity") on a line of n_m0 output traces
 (CMPs) x n_t0 samples, domains laid out m0-major (d = c n_t0 + t). The line
@@ -19,7 +19,7 @@ Sec. 4); buckets are independent and every bucket runs the same stages:
   N_skip = 0, 1, 2). Each estimated sample starts from NP_bf individuals: the
   bests of samples t-1 and t+1 on the same trace, the best of sample t on the
   previous trace of the sweep (absent on the sweep's first trace), and its
-  own best (Sec. 3.4, the four seeds), the remaining members random; it is
+  own best (Sec. 3.3, the four seeds), the remaining members random; it is
   evolved for NG_bf generations;
 * after the estimated samples of a trace, every other sample of that trace is
   interpolated linearly in t between the bests of the nearest estimated
@@ -91,10 +91,22 @@ def interpolate(t, est_sorted, theta_of):
     return (a + f32(w * f32(b - a))).astype(f32)
 
 
-def ens_search(traces, mid, off, prob, cfg):
+def ens_search(traces, mid, off, prob, cfg, fitness=None):
     """Run ENS over the m0-major grid of ``prob`` with settings ``cfg``
     (attributes np, ng [= NP_f, NG_f], np_bf, ng_bf, n_skip, n_cycle,
-    n_bucket, F, CR, seed, lo, hi). Returns (best_theta, best_S, n_calls)."""
+    n_bucket, F, CR, seed, lo, hi). Returns (best_theta, best_S, n_calls).
+
+    ``fitness(theta [n, P, D] float32, domains) -> float32 [n, P]`` gives
+    the semblance of each parameter vector at its domain; by default the
+    FP64 semblance rounded to FP32. Every decision of the sweep (selection,
+    arg-max, keep-if-higher) is taken on these values, so a caller can pass
+    another evaluation of the same semblance -- e.g. the FP32 values of an
+    implementation under test -- and compare the sweeps step by step on
+    identical fitness (FP32 and FP64 semblances round differently and can
+    rank two members in opposite orders)."""
+    if fitness is None:
+        def fitness(theta, domains):
+            return semblance_many(traces, mid, off, prob, theta, domains=domains).astype(f32)
     n_m0, n_t0 = prob.n_m0, prob.n_t0
     D = len(cfg.lo)
     lo = np.asarray(cfg.lo, f32)
@@ -146,7 +158,7 @@ def ens_search(traces, mid, off, prob, cfg):
                 for i in range(NP):
                     pop[r, i] = seeds[i] if i < len(seeds) else de_mod.init_individual(
                         cfg.seed, d, i, lo, hi, gen=gen_code(s, 0))
-            fit = semblance_many(traces, mid, off, prob, pop, domains=doms).astype(f32)
+            fit = np.asarray(fitness(pop, doms), f32)
             n_calls += len(doms) * (NP if kind == "explore" else NP - 1)
             adapt = bool(getattr(cfg, "adapt", 0))
             states = [jade.new_state(NP, D, cfg.F, cfg.CR) for _ in doms] if adapt else None
@@ -160,7 +172,7 @@ def ens_search(traces, mid, off, prob, cfg):
                         trial[r], _ = de_mod.mutate_population(cfg.seed, d, gen_code(s, g),
                                                               pop[r], fit[r], cfg.F, cfg.CR, lo,
                                                               hi)
-                tfit = semblance_many(traces, mid, off, prob, trial, domains=doms).astype(f32)
+                tfit = np.asarray(fitness(trial, doms), f32)
                 n_calls += len(doms) * NP
                 for r, d in enumerate(doms):
                     if adapt:
@@ -176,8 +188,7 @@ def ens_search(traces, mid, off, prob, cfg):
                 idoms = [c * n_t0 + t for c in cmps for t in skipped]
                 ith = np.stack([interpolate(d % n_t0, est, lambda tt, c=d // n_t0:
                                             best_th[c * n_t0 + tt]) for d in idoms])
-                iS = semblance_many(traces, mid, off, prob, ith[:, None, :],
-                                    domains=idoms)[:, 0].astype(f32)
+                iS = np.asarray(fitness(ith[:, None, :], idoms), f32)[:, 0]
                 n_calls += len(idoms)
                 for r, d in enumerate(idoms):
                     if de_mod.rank_key(iS[r]) > de_mod.rank_key(best_S[d]):

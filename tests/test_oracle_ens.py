@@ -112,7 +112,7 @@ def test_ens_beats_jade_at_equal_cost_and_recovers(adapt):
 
 def test_exploration_carries_each_bucket_first_trace():
     """With one member and no generations the exploration stage is pure
-    propagation (Sec. 3.4, previous-trace seed): the first trace of each
+    propagation (Sec. 3.3, previous-trace seed): the first trace of each
     bucket draws a random member per sample (keyed by its own domain, slot 0,
     the stage's generation code), and every later trace of the bucket starts
     from -- and keeps -- the best of the same sample on the previous trace.
@@ -139,7 +139,7 @@ def test_exploration_carries_each_bucket_first_trace():
 
 def test_cycles_never_lower_a_sample():
     """Backward-and-forward cycles seed every estimated sample with its own
-    best among the four seeds (Sec. 3.4), selection is elitist and an
+    best among the four seeds (Sec. 3.3), selection is elitist and an
     interpolated value replaces a best only when higher (Sec. 3.5), so the
     semblance of every sample after the cycles is at least its value after
     the exploration stage -- and the cycles raise many of them."""
@@ -149,3 +149,31 @@ def test_cycles_never_lower_a_sample():
     _, S_c, _ = ens.ens_search(wl.traces, wl.mid, wl.off, prob, EnsCfg(n_cycle=2, n_bucket=4))
     assert np.all(S_c >= S_x)
     assert np.mean(S_c > S_x) > 0.3
+
+
+@pytest.mark.parametrize("adapt", [0, 1])
+def test_every_decision_uses_the_supplied_fitness(adapt):
+    """The sweep's decisions (selections, arg-maxes, keep-if-higher) depend
+    only on the order of the fitness values, and every evaluation goes
+    through the supplied fitness: halving every value (exact in FP32, order
+    and ties kept) leaves the bests' parameters unchanged and halves every
+    reported semblance; a fitness that reverses the order changes them."""
+    wl = configs.crs_line(2, n_cmp=5, ns=60, n_events=2, ap_half=2, tau_max=0.22)
+    cfg = EnsCfg(ng=2, ng_bf=1, n_skip=1, n_bucket=3, adapt=adapt, CR=0.5 if adapt else 0.9)
+    base = ens.ens_search(wl.traces, wl.mid, wl.off, wl.problem, cfg)
+
+    def halved(theta, domains):
+        return (semblance_many(wl.traces, wl.mid, wl.off, wl.problem, theta, domains=domains)
+                .astype(f32) * f32(0.5))
+
+    th, S, n = ens.ens_search(wl.traces, wl.mid, wl.off, wl.problem, cfg, fitness=halved)
+    assert n == base[2]
+    assert np.array_equal(th, base[0])
+    assert np.array_equal(S, base[1] * f32(0.5))
+
+    def reversed_(theta, domains):
+        return -semblance_many(wl.traces, wl.mid, wl.off, wl.problem, theta,
+                               domains=domains).astype(f32)
+
+    th_r, _, _ = ens.ens_search(wl.traces, wl.mid, wl.off, wl.problem, cfg, fitness=reversed_)
+    assert not np.array_equal(th_r, base[0])
