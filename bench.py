@@ -16,6 +16,14 @@ per-GPU work is fixed and scaling is weak. Rank 0 prints one JSON line.
 
 --impl reference times the CPU oracle (FP64 semblance, FP32 DE) on the host
 cores instead, each step a bounded sample of the same workload.
+
+Beside the headline line (rank 0, N = 1) the JSON carries a `comparison`:
+the same search in its plain FP32 form (scalar kernel, no polish) and with
+BF16-stored traces; the large line's central 100-CMP slab with BF16 and
+FP32 storage and the error of its reported S against the FP64 oracle on a
+1% sample of domains; and the 4096-problem batched workload with the
+autotuned kernel against the scalar one. --paper-compare adds a re-run of
+the paper's ENS-versus-JADE experiment (context only).
 """
 from __future__ import annotations
 
@@ -34,11 +42,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ZO samples solved/s (CRS search with neighbour exchange + gradient polish)"
 UNIT = "ZO samples/s"
-# algorithmic FP32 flops per (trace, parameter vector) pair of K1 (an FMA
-# counts 2; the square root and its clamp 1 each): traveltime 9 (CRS; CMP 5,
-# FO-CRS 15), interpolation 33, stack 11, energy 22
+# Algorithmic FP32 work per (trace, parameter vector) pair of K1, two counts:
+#  * flops, an FMA counting 2 and the square root and its clamp 1 each:
+#    traveltime 9 (CRS; CMP 5, FO-CRS 15), interpolation 33, stack 11,
+#    energy 22 -> 75 for CRS;
+#  * operations, an FMA counting 1 (the count 8 + 4 (2w + 1) + 1 square root
+#    = 53 for CRS at w = 5: traveltime 8, per window sample an interpolation
+#    product and FMA, a stack add and an energy FMA).
 FLOPS_PER_TRACE_EVAL = {0: 71, 1: 75, 2: 81}  # by operator: CMP, CRS, FO-CRS
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+OPS_PER_TRACE_EVAL = {0: 49, 1: 53, 2: 59}
+FP32_LANES = 128          # FP32 lanes per SM (an FMA per lane per clock)
+L1_BYTES_PER_CLK = 128    # L1 / shared-memory data path per SM per clock
 
 
 def workload_config(wl, n_gpus):
@@ -90,19 +104,24 @@ def job_value(n_dom_per_rank: int, world: int, seconds_per_step: float) -> float
 # ------------------------------------------------------------------ accuracy
 
 def recovery(wl, best_theta, tol=0.01):
-    """Fraction of event-centred domains (isolated strong events, truth in
-    bounds) whose recovered A (as a fraction of its range) and C (relative)
-    are within ``tol`` of the exact recentred parameters, and their count."""
+    """Recovered CRS parameters at event-centred domains (isolated strong
+    events, truth in bounds) against the exact recentred values: how many
+    have A and B within ``tol`` of their bound ranges, C within ``tol``
+    relative, and all three at once. B's effect on the data is tiny at these
+    apertures, so its error is also given as the traveltime shift it causes
+    at the aperture's farthest midpoint, |dB| dm_max^2 / (2 t0), in samples
+    (median and maximum over the domains)."""
     import synth
     prob, line = wl.problem, wl.line
     if line is None or prob.n_m0 * prob.n_t0 != prob.n_dom:
         return None
     lo, hi = np.array(wl.de.lo), np.array(wl.de.hi)
     ev = line.events
-    hits = tried = 0
+    hits = {"A": 0, "B": 0, "C": 0, "all": 0}
+    tried, shift, b_range_shift = 0, [], []
     for e in range(len(ev)):
         c = int(np.argmin(np.abs(line.cmp_x - ev[e, 0])))
-        if c < 15 or c > line.n_cmp - 16 or c >= prob.n_m0 or abs(ev[e, 5]) < 0.7:
+        if c < 15 or c > line.n_cmp - 16 or abs(ev[e, 5]) < 0.7:
             continue
         truth = synth.crs_recentre(ev[e], line.cmp_x[c])
         if truth is None or not (lo[0] < truth[1] < hi[0] and lo[2] < truth[3] < hi[2]):
@@ -112,11 +131,33 @@ def recovery(wl, best_theta, tol=0.01):
         if it < 20 or it > prob.n_t0 - 20 or any(o is not None and abs(o[0] - truth[0]) < 0.1
                                                  for o in others):
             continue
-        d = c * prob.n_t0 + it
+        # the domain of (CMP c, sample it); c indexes the line, and the
+        # problem may solve a slab of it
+        rows = np.nonzero(np.abs(prob.group_m0 - line.cmp_x[c]) < 1e-3)[0]
+        cand = np.nonzero(np.isin(prob.dom_group, rows) & (prob.dom_it0 == it))[0]
+        if cand.size == 0:
+            continue  # the CMP lies outside the solved slab
+        d = int(cand[0])
+        g = int(prob.dom_group[d])
+        idx = prob.ap_idx[prob.ap_ptr[g]:prob.ap_ptr[g + 1]]
+        dm_max = float(np.max(np.abs(wl.mid[idx] - prob.group_m0[g]))) if idx.size else 0.0
         tried += 1
-        hits += int(abs(best_theta[d, 0] - truth[1]) <= tol * (hi[0] - lo[0])
-                    and abs(best_theta[d, 2] - truth[3]) <= tol * truth[3])
-    return {"within_1pct": hits, "of": tried}
+        ok_a = abs(best_theta[d, 0] - truth[1]) <= tol * (hi[0] - lo[0])
+        ok_b = abs(best_theta[d, 1] - truth[2]) <= tol * (hi[1] - lo[1])
+        ok_c = abs(best_theta[d, 2] - truth[3]) <= tol * truth[3]
+        hits["A"] += int(ok_a)
+        hits["B"] += int(ok_b)
+        hits["C"] += int(ok_c)
+        hits["all"] += int(ok_a and ok_b and ok_c)
+        shift.append(abs(best_theta[d, 1] - truth[2]) * dm_max ** 2 / (2 * truth[0]) / wl.dt)
+        b_range_shift.append((hi[1] - lo[1]) * dm_max ** 2 / (2 * truth[0]) / wl.dt)
+    out = {"within_1pct": hits, "of": tried,
+           "rule": "A, B: 1% of the bound range; C: 1% relative"}
+    if shift:
+        out["B_edge_shift_samples"] = {"median": float(np.median(shift)),
+                                       "max": float(np.max(shift)),
+                                       "whole_B_range_median": float(np.median(b_range_shift))}
+    return out
 
 
 def fo_recovery(wl, best_theta):
@@ -202,6 +243,110 @@ def paper_compare(tt, wl, dev, stream, runs=None, recover=None):
         out["jade_80x80_over_ens_80x80_time"] = (out["jade_80x80"]["seconds"] /
                                                  out["ens_80x80"]["seconds"])
     return out
+
+
+# ------------------------------------------------------------------ other workloads
+
+def _timed_search(tt, ctx, stream, out_t=None, out_s=None):
+    """One tt_search timed with CUDA events on the launching stream (the
+    caller has warmed the kernels); returns (seconds, best_theta, best_S)."""
+    import torch
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    th, S, _ = tt.tt_search(ctx, out_t, out_s)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3, th, S
+
+
+def _autotune(tt, ctx, n_dom, np_, D, dev):
+    import torch
+    th = torch.empty((n_dom, np_, D), dtype=torch.float32, device=dev)
+    tt.tt_de_step(ctx, 0, th)
+    tuned = {f"{k}/{b}": round(v, 3) for (k, b), v in tt.tt_ctx_autotune(ctx, th).items()}
+    del th
+    return tuned, f"{tt.tt_ctx_get_option(ctx, 'kernel')}/{tt.tt_ctx_get_option(ctx, 'block')}"
+
+
+def large_slab_compare(tt, dev, stream, n_slab=100, sample_frac=0.01):
+    """The large line (2000 CMPs x 120 offsets x 2000 samples at 2 ms, 60
+    events, SNR 2, aperture +-25 CMPs, DE 96 x 120 with exchange and polish):
+    the central n_slab-CMP slab solved with BF16-stored and with FP32-stored
+    traces (each autotuned, one timed search), ZO samples/s and recovery of
+    each, and the error of the reported S against the FP64 oracle on a seeded
+    sample of sample_frac of the slab's domains: against the FP32 record
+    (what BF16 storage costs, bar 2e-3) and, for BF16, against the
+    BF16-rounded record (the arithmetic alone, bar 1e-5)."""
+    import oracle
+    import torch
+    from synth import configs
+    c0 = 1000 - n_slab // 2
+    wl = configs.large_line(0, cmps=list(range(c0, c0 + n_slab)))
+    prob = wl.problem
+    rng = np.random.default_rng(5)
+    doms = np.sort(rng.choice(prob.n_dom, max(1, int(round(sample_frac * prob.n_dom))),
+                              replace=False))
+    out = {"workload": f"large line 2000 CMP x 120 x 2000 (dt 2 ms), central {n_slab}-CMP "
+                       f"slab ({prob.n_dom} domains), aperture +-25 CMP, DE "
+                       f"{wl.de.np} x {wl.de.ng}, exchange every {wl.de.exch_every}, "
+                       f"{wl.de.polish_steps} polish steps",
+           "s_error_sample": f"{doms.size} domains ({100 * sample_frac:g}% of the slab, seed 5)"}
+    bf16_rec = None
+    for storage in ("bf16", "f32"):
+        ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, storage=storage,
+                               device=dev)
+        tuned, kern = _autotune(tt, ctx, prob.n_dom, wl.de.np, ctx.D, dev)
+        secs, th, S = _timed_search(tt, ctx, stream)
+        th, S = th.cpu().numpy(), S.cpu().numpy()
+        ctx.close()
+        ref = oracle.semblance.semblance_many(wl.traces, wl.mid, wl.off, prob,
+                                              th[doms][:, None, :], domains=doms)[:, 0]
+        err = np.abs(S[doms] - ref)
+        e = {"value": prob.n_dom / secs, "seconds": secs, "kernel": kern,
+             "recovery": recovery(wl, th),
+             "s_error_vs_fp64_oracle": {"max": float(err.max()), "median": float(np.median(err)),
+                                        "record": "FP32"}}
+        if storage == "bf16":
+            if bf16_rec is None:
+                bf16_rec = torch.from_numpy(wl.traces).to(torch.bfloat16).to(
+                    torch.float32).numpy()
+            ref_b = oracle.semblance.semblance_many(bf16_rec, wl.mid, wl.off, prob,
+                                                    th[doms][:, None, :], domains=doms)[:, 0]
+            err_b = np.abs(S[doms] - ref_b)
+            e["s_error_vs_fp64_oracle_bf16_record"] = {"max": float(err_b.max()),
+                                                       "median": float(np.median(err_b))}
+        out[f"{storage}_stored"] = e
+    out["bf16_over_f32"] = out["bf16_stored"]["value"] / out["f32_stored"]["value"]
+    return out
+
+
+def batched_compare(tt, dev, stream):
+    """The batched workload (4096 uneven CRS problems, 16-240 traces and
+    750-3000 samples at 2 or 4 ms each, every sample a domain, DE 64 x 80):
+    one timed search with the autotuned kernel (the persistent work queue
+    for these uneven apertures) against the plain form (scalar kernel, one
+    pair per thread, grid-mapped), on the same context and inputs; the two
+    give identical results, so they are at the same accuracy."""
+    from synth import configs
+    wl = configs.batched(0)
+    prob = wl.problem
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, prob, wl.de, device=dev)
+    tuned, kern = _autotune(tt, ctx, prob.n_dom, wl.de.np, ctx.D, dev)
+    secs, th_a, _ = _timed_search(tt, ctx, stream)
+    th_a = th_a.cpu().numpy()
+    tt.tt_ctx_set_option(ctx, "kernel", "scalar")
+    tt.tt_search(ctx)  # capture the scalar form's graph
+    secs_s, th_s, _ = _timed_search(tt, ctx, stream)
+    same = bool(np.array_equal(th_a, th_s.cpu().numpy()))
+    ctx.close()
+    return {"workload": f"{prob.n_groups} uneven CRS problems (16-240 traces, 750-3000 "
+                        f"samples, dt 2/4 ms), {prob.n_dom} domains, DE {wl.de.np} x {wl.de.ng}",
+            "autotuned": {"value": prob.n_dom / secs, "seconds": secs, "kernel": kern,
+                          "autotune_ms": tuned},
+            "plain_scalar": {"value": prob.n_dom / secs_s, "seconds": secs_s,
+                             "kernel": "scalar (one pair per thread, grid-mapped)"},
+            "speedup": secs_s / secs, "identical_results": same}
 
 
 # ------------------------------------------------------------------ clocks
@@ -355,6 +500,77 @@ def l2_probe(dev, stream):
                                    "20 copies per CUDA graph, 5 replays, read + write bytes"}
 
 
+def device_counts(ctx_sm):
+    """(SM count, maximum SM clock in MHz and where it came from): the SM
+    count is the library's query of the device; the clock is nvidia-smi's
+    clocks.max.sm, else the measured-peaks file's sm_max_mhz."""
+    mhz, src = None, None
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,"
+                              "nounits", "-i", os.environ.get("LOCAL_RANK", "0")],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        mhz, src = float(out.splitlines()[0]), "nvidia-smi clocks.max.sm"
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz, src = float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+        except (OSError, KeyError, ValueError):
+            mhz, src = None, "unknown"
+    return int(ctx_sm), mhz, src
+
+
+def roofline(tt, ctx, prob, stats, args, clk):
+    """Roofline of K1 from the library's live CUDA-event timing of every
+    semblance launch in the timed steps. The headline bound is the on-chip
+    data path that K1's window loads go through: every (trace, vector) pair
+    gathers 2w + 2 samples (48 B in FP32, 24 B in BF16), and the L1 /
+    shared-memory data path moves 128 B per clock per SM, so
+      peak = n_sm x 128 B x max SM clock,
+      achieved = pairs per launch x bytes per pair / mean launch time,
+    both printed with the SM count and clock they use. Beside it: the FP32
+    pipe (n_sm x 128 lanes x 2 flops x clock) under the two work counts, and
+    the DRAM bytes of one launch from an ncu capture (traffic)."""
+    n_sm, mhz, mhz_src = device_counts(tt.tt_ctx_get_option(ctx, "sm_count"))
+    if mhz is None:
+        mhz = clk.get("sm_max_mhz") or 0.0
+    w = int(prob.half_window)
+    bytes_pair = (2 * w + 2) * (2 if args.storage == "bf16" else 4)
+    ms_launch = stats["semblance_ms"] / stats["timed_launches"]
+    pairs_launch = stats["trace_evals"] / stats["semblance_launches"]
+    pairs_s = pairs_launch / (ms_launch / 1e3)
+    achieved = pairs_s * bytes_pair / 1e9
+    peak = n_sm * L1_BYTES_PER_CLK * mhz * 1e6 / 1e9
+    kern = f"{tt.tt_ctx_get_option(ctx, 'kernel')}/{tt.tt_ctx_get_option(ctx, 'block')}"
+    traffic = (K1_LINE_DRAM_BYTES if (args.workload == "line" and args.storage == "f32" and
+                                      not args.cmps and kern == K1_LINE_DRAM_KERNEL) else None)
+    fp32_peak = n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    op = int(prob.op)
+    roof = {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "kernel": f"k_semblance ({kern})",
+            "peak_source": (f"derived: {n_sm} SMs (device query) x {L1_BYTES_PER_CLK} B/clk x "
+                            f"{mhz:.0f} MHz ({mhz_src})"),
+            "sm_count": n_sm, "sm_max_mhz": mhz, "bytes_per_pair": bytes_pair,
+            "pairs_per_launch": pairs_launch, "per_launch_ms": ms_launch,
+            "trace_evals_per_s": pairs_s, "trace_samples_per_s": pairs_s * (2 * w + 1),
+            "semblance_share_of_step": None,
+            "fp32": {"peak_tflops": fp32_peak,
+                     "flops_fma2": {"per_pair": FLOPS_PER_TRACE_EVAL[op],
+                                    "tflops": pairs_s * FLOPS_PER_TRACE_EVAL[op] / 1e12,
+                                    "frac": pairs_s * FLOPS_PER_TRACE_EVAL[op] / 1e12 / fp32_peak},
+                     "ops_fma1": {"per_pair": OPS_PER_TRACE_EVAL[op],
+                                  "tops": pairs_s * OPS_PER_TRACE_EVAL[op] / 1e12,
+                                  "peak_tops": fp32_peak / 2,
+                                  "frac": pairs_s * OPS_PER_TRACE_EVAL[op] / 1e12 /
+                                  (fp32_peak / 2)}}}
+    # the gathered samples as a byte rate beside the HBM copy bandwidth: L1
+    # serves them, at several times what HBM could deliver
+    hbm, src = hbm_peak_gbs()
+    roof["gathered"] = {"gbs": achieved, "hbm_gbs": hbm, "hbm_source": src,
+                        "over_hbm": achieved / hbm}
+    return roof
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,8 +581,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-FP32 and BF16-stored comparison searches")
-    ap.add_argument("--no-paper-compare", action="store_true",
-                    help="skip the ENS-vs-JADE comparison of the paper's experiment")
+    ap.add_argument("--paper-compare", action="store_true",
+                    help="also re-run the paper's ENS-vs-JADE experiment on the line (context, "
+                         "off by default)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large-line slab comparison (BF16 vs FP32 storage, S error "
+                         "against the FP64 oracle on a 1%% sample)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-workload comparison (autotuned vs scalar kernel)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--cmps", type=int, default=0,
                     help="solve only the first CMPS midpoints of the line (profiling case)")
@@ -481,36 +703,10 @@ def main():
                "d2h_bytes_per_step": int(host_bt.numel() * 4 + host_bs.numel() * 4)}
 
     # roofline of the dominant kernel (semblance), from its live launch times
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roof = None
     if stats["timed_launches"] > 0 and stats["semblance_ms"] > 0:
-        flops = stats["trace_evals"] * FLOPS_PER_TRACE_EVAL[int(prob.op)]
-        n_l = stats["semblance_launches"]
-        achieved = (flops / n_l) / (stats["semblance_ms"] / stats["timed_launches"] / 1e3) / 1e12
-        kern = f"{tt.tt_ctx_get_option(ctx, 'kernel')}/{tt.tt_ctx_get_option(ctx, 'block')}"
-        traffic = (K1_LINE_DRAM_BYTES if (args.workload == "line" and args.storage == "f32" and
-                                          not args.cmps and kern == K1_LINE_DRAM_KERNEL) else None)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_semblance (FP32 FMA pipe; peak = 152 SM x 128 lanes x 2 x 2070 MHz)",
-                "per_launch_ms": stats["semblance_ms"] / stats["timed_launches"],
-                "trace_evals_per_s": stats["trace_evals"] / (stats["semblance_ms"] / 1e3),
-                "semblance_share_of_step": stats["semblance_ms"] / ms}
-        # the on-chip bound: each pair moves 2w+2 samples through the L1 data
-        # path, 128 B per clock per SM
-        w = int(prob.half_window)
-        bytes_pair = (2 * w + 2) * (2 if args.storage == "bf16" else 4)
-        l1_peak = SM_COUNT * 128.0 * SM_MAX_MHZ * 1e6 / bytes_pair
-        roof["l1"] = {"bytes_per_pair": bytes_pair, "peak_pairs_per_s": l1_peak,
-                      "frac": roof["trace_evals_per_s"] / l1_peak}
-        # semblance trace-samples per second: pairs x window length
-        roof["trace_samples_per_s"] = roof["trace_evals_per_s"] * (2 * w + 1)
-        # the gathered samples as a byte rate, beside the HBM copy bandwidth:
-        # L1 serves them, at several times what HBM could deliver
-        hbm, src = hbm_peak_gbs()
-        gathered = roof["trace_evals_per_s"] * bytes_pair / 1e9
-        roof["gathered"] = {"gbs": gathered, "hbm_gbs": hbm, "hbm_source": src,
-                            "over_hbm": gathered / hbm}
+        roof = roofline(tt, ctx, prob, stats, args, clk)
+        roof["semblance_share_of_step"] = stats["semblance_ms"] / ms
         if rank == 0:
             roof["l2_probe"] = l2_probe(dev, stream)
     # the same search in other forms on the same GPU (rank 0, line workload)
@@ -548,7 +744,11 @@ def main():
         one_form("bf16_stored", "bf16", "packed", wl.de.polish_steps,
                  "BF16 trace copy, FP32 arithmetic, FP64 chunked energy, polish")
         comparison["speedup_vs_plain_fp32"] = value / comparison["plain_fp32"]["value"]
-        if not args.no_paper_compare:
+        if not args.no_large:
+            comparison["large_line_slab"] = large_slab_compare(tt, dev, stream)
+        if not args.no_batched:
+            comparison["batched"] = batched_compare(tt, dev, stream)
+        if args.paper_compare:
             comparison["paper_ens_vs_jade"] = paper_compare(tt, wl, dev, stream)
             # the paper's experiments use FO-CRS on a common-offset 1000 m panel
             import synth

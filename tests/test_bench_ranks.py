@@ -64,7 +64,8 @@ def test_single_rank_helpers():
 
 def test_recovery_metric_counts_exact_truth():
     """bench.recovery: the exact recentred parameters at every domain count
-    as recovered; a 2% error in C does not."""
+    as recovered in A, B and C; a 2% error in C, or an error of 2% of B's
+    bound range, does not (and only the parameter it was put in fails)."""
     sys.path.insert(0, ROOT)
     import numpy as np
     import bench
@@ -82,6 +83,12 @@ def test_recovery_metric_counts_exact_truth():
             if 0 <= it < p.n_t0:
                 th[c * p.n_t0 + it] = (tr[1], tr[2], tr[3])
     r = bench.recovery(wl, th)
-    assert r is not None and r["of"] >= 1 and r["within_1pct"] == r["of"]
+    n = r["of"]
+    assert r is not None and n >= 1
+    assert r["within_1pct"] == {"A": n, "B": n, "C": n, "all": n}
+    assert r["B_edge_shift_samples"]["max"] < 1e-6
+    tb = th.copy()
+    tb[:, 1] += 0.02 * (configs.CRS_HI[1] - configs.CRS_LO[1])
+    assert bench.recovery(wl, tb)["within_1pct"] == {"A": n, "B": 0, "C": n, "all": 0}
     th[:, 2] *= 1.02
-    assert bench.recovery(wl, th)["within_1pct"] == 0
+    assert bench.recovery(wl, th)["within_1pct"] == {"A": n, "B": n, "C": 0, "all": 0}

@@ -5,8 +5,9 @@ parameters at event-centred domains.
 Search trajectories of the FP32 GPU path and the FP64 oracle part once two
 semblance values differ below 1e-5, so end-to-end parity is assessed by the
 recovered parameters (within 1% of the generating values: relative for C,
-a fraction of the bound range for A) and by re-evaluating the reported
-optimum with the oracle; step-level parity is bit-exact (test_gpu_de).
+a fraction of the bound range for A and B; B only on apertures wide enough
+to resolve it) and by re-evaluating the reported optimum with the oracle;
+step-level parity is bit-exact (test_gpu_de).
 """
 import numpy as np
 import pytest
@@ -85,6 +86,36 @@ def test_crs_search_with_exchange_and_polish():
         assert bt[d, 2] == pytest.approx(truth[3], rel=0.01)
         ok += 1
     assert ok == 5
+
+
+def test_crs_search_recovers_B_where_the_aperture_resolves_it():
+    """B (the CRS curvature in dm^2) moves a trace by |dB| dm^2 / (2 t0):
+    on a +-10-CMP aperture (+-125 m) its whole bound range shifts the
+    aperture edge by about a quarter sample, below what semblance resolves
+    (there S is flat within 1e-3 over 30% of B's range even at the true A
+    and C), so B is checked on the +-25-CMP aperture of the large-line
+    workload (+-312.5 m), where S peaks within 1% of B's range of the truth:
+    A, B (fractions of their bound ranges) and C (relative) within 1% at the
+    event's zero-offset sample of three central CMPs."""
+    wl = configs.crs_line(39, n_cmp=61, ns=300, n_events=1, ap_half=25, np_=48, ng=80,
+                          exch_every=10, polish_steps=5, snr=20.0, tau_max=0.9)
+    ev = wl.line.events[0]
+    c_ev = int(np.argmin(np.abs(wl.line.cmp_x - ev[0])))
+    cs = [c for c in (c_ev - 1, c_ev, c_ev + 1) if 25 <= c < 61 - 25]
+    assert cs
+    truths = {c: synth.crs_recentre(ev, wl.line.cmp_x[c]) for c in cs}
+    its = sorted(int(round(t[0] / wl.dt)) for t in truths.values())
+    wl.problem = synth.line_problem(wl.line, half_window=5, ap_half=25, cmps=cs,
+                                    t0_range=(its[0] - 4, its[-1] + 5))
+    prob = wl.problem
+    bt, bs, n = _run(wl)
+    lo, hi = np.array(wl.de.lo), np.array(wl.de.hi)
+    for k, c in enumerate(cs):
+        truth = truths[c]
+        d = k * prob.n_t0 + int(round(truth[0] / wl.dt)) - (its[0] - 4)
+        assert abs(bt[d, 0] - truth[1]) <= 0.01 * (hi[0] - lo[0]), (c, bt[d], truth)
+        assert abs(bt[d, 1] - truth[2]) <= 0.01 * (hi[1] - lo[1]), (c, bt[d], truth)
+        assert bt[d, 2] == pytest.approx(truth[3], rel=0.01), (c, bt[d], truth)
 
 
 def test_search_matches_oracle_quality_small():
