@@ -10,9 +10,13 @@ L2).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 (launched by torchrun): every rank solves its own independent line
-(a replica with its own seed; the search has no cross-line exchange), so
-per-GPU work is fixed and scaling is weak. Rank 0 prints one JSON line.
+N > 1 (launched by torchrun): the line is cut into N contiguous slabs of
+CMPs, one per rank (tt_search_slab): each GPU holds its slab's traces plus
+a read-only halo of the aperture radius, and at every exchange generation
+the ranks swap the bests of their edge rows by NCCL point-to-point; the
+slabs together solve the same line, so scaling is strong. (The other
+workloads run as independent replicas per rank, weak scaling.) Rank 0 prints
+one JSON line.
 
 --impl reference times the CPU oracle (FP64 semblance, FP32 DE) on the host
 cores instead, each step a bounded sample of the same workload.
@@ -74,7 +78,9 @@ def workload_config(wl, n_gpus):
             "n_dom": p.n_dom, "np": wl.de.np, "ng": wl.de.ng, "exch_every": wl.de.exch_every,
             "polish_steps": wl.de.polish_steps, "storage": wl.storage,
             "l2": "flushed between timed steps (256 MiB write)",
-            "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "1 GPU"}
+            "parallelism": ("1 GPU" if n_gpus == 1 else
+                            f"midpoint slabs x{n_gpus} (edge-row exchange)"
+                            if getattr(wl, "slab", None) else f"replicas x{n_gpus}")}
 
 
 # ------------------------------------------------------------------ ranks
@@ -93,6 +99,17 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     import torch.distributed as dist
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int, device=None) -> float:
+    """The sum of a value over the ranks (whole-job counts)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -645,7 +662,23 @@ def main():
         import synth
         wl.problem = synth.line_problem(wl.line, half_window=5, ap_half=10,
                                         cmps=list(range(args.cmps)))
+    slab = None
+    if world > 1 and args.workload == "line":
+        # one slab of the same line per rank, with its aperture halo
+        import synth
+        from paper_2304_11399_gb300.slab import halo_exchange
+        wl = configs.crs_line(0)
+        c0, c1 = synth.slab_bounds(wl.problem.n_m0, world, rank)
+        wl.traces, wl.mid, wl.off, wl.problem, base, hp, hn = synth.slab_problem(
+            wl.line, c0, c1, half_window=5, ap_half=10)
+        slab = (base, hp, hn, halo_exchange(rank, world))
+        wl.slab = (c0, c1)
     prob = wl.problem
+
+    def search(ctx, best_t, best_s):
+        if slab is None:
+            return tt.tt_search(ctx, best_t, best_s)
+        return tt.tt_search_slab(ctx, *slab, best_theta=best_t, best_S=best_s)
     # CPU baseline first (rank 0, N = 1): the oracle as it stands on a sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "line":
@@ -674,7 +707,7 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        tt.tt_search(ctx, best_t, best_s)
+        search(ctx, best_t, best_s)
     barrier()
     tt.tt_ctx_profile(ctx, True)
     tt.tt_ctx_stats(ctx, reset=True)
@@ -687,7 +720,7 @@ def main():
     for k in range(args.steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
-        _, _, n_evals = tt.tt_search(ctx, best_t, best_s)
+        _, _, n_evals = search(ctx, best_t, best_s)
         ev[k][1].record(stream)
     barrier()
     clk = clocks.stop()
@@ -696,7 +729,11 @@ def main():
     tt.tt_ctx_profile(ctx, False)
     ms_max = max_over_ranks(ms, world, dev)
     per_step_s = ms_max / 1e3 / args.steps
-    value = job_value(prob.n_dom, world, per_step_s)
+    # whole-job ZO samples: every rank's own line (replicas) or the slabs
+    # of one line
+    n_total = prob.n_dom * world if slab is None else int(sum_over_ranks(prob.n_dom, world,
+                                                                         dev))
+    value = n_total / per_step_s
 
     # end to end through the public API with host buffers
     e2e = None
@@ -708,15 +745,16 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             tt.tt_ctx_load_traces(ctx, host_tr)
-            tt.tt_search(ctx, best_t, best_s)
+            search(ctx, best_t, best_s)
             host_bt.copy_(best_t, non_blocking=True)
             host_bs.copy_(best_s, non_blocking=True)
             torch.cuda.synchronize()
         barrier()
         e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-        e2e = {"value": job_value(prob.n_dom, world, e_s / args.steps), "unit": UNIT,
-               "h2d_bytes_per_step": int(wl.traces.nbytes),
-               "d2h_bytes_per_step": int(host_bt.numel() * 4 + host_bs.numel() * 4)}
+        e2e = {"value": n_total / (e_s / args.steps), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum_over_ranks(wl.traces.nbytes, world, dev)),
+               "d2h_bytes_per_step": int(sum_over_ranks(host_bt.numel() * 4 +
+                                                        host_bs.numel() * 4, world, dev))}
 
     # roofline of the dominant kernel (semblance), from its live launch times
     roof = None
@@ -727,7 +765,7 @@ def main():
             roof["l2_probe"] = l2_probe(dev, stream)
     # the same search in other forms on the same GPU (rank 0, line workload)
     comparison = None
-    if rank == 0 and args.workload == "line" and not args.no_compare:
+    if rank == 0 and world == 1 and args.workload == "line" and not args.no_compare:
         import copy
         torch.cuda.synchronize()
         comparison = {"optimised_fp32": {"value": value,
@@ -780,7 +818,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_s * 1e3,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": "strong" if slab else "weak",
+                "vs_baseline": None,
                 "dtype": "f32" if args.storage == "f32" else "bf16-stored/f32",
                 "data": "synthetic (seeded Ricker events + Gaussian noise, SNR 3)",
                 "config": workload_config(wl, world), "clocks": clk, "e2e": e2e,

@@ -367,6 +367,48 @@ tt_status tt_ctx_autotune(tt_ctx* ctx, const float* theta, int32_t P, float* S,
 tt_status tt_search(tt_ctx* ctx, float* best_theta, float* best_S, uint64_t* n_evals,
                     void* stream);
 
+/* One slab of a search sharded over several GPUs by midpoint (Sec. 4: the
+ * data is cut into buckets processed independently; Sec. 5.5: the buckets
+ * run on up to 16 GPUs). A long line is cut into contiguous slabs of CMPs,
+ * one per GPU; each GPU's context holds its slab's domains (an m0-major
+ * n_m0 x n_t0 grid) over a copy of only the traces their apertures read
+ * (the slab plus a read-only halo of the aperture radius). The slabs share
+ * one thing: at every exchange generation, the neighbour exchange of the
+ * first (last) row of a slab imports the bests of the previous (next)
+ * slab's last (first) row. The library writes its own edge rows to
+ * send_first / send_last and then calls `exchange`, which must fill
+ * recv_prev / recv_next with the neighbouring slabs' rows of the same
+ * generation -- by NCCL send/recv into this GPU's own memory, by host
+ * staging, or otherwise -- before returning, or enqueue that on `stream`
+ * (the library's next launch on `stream` reads them). With dom_base the
+ * global index of the slab's first domain on the whole line's grid (its
+ * Philox keys), the slabs together compute exactly what tt_search computes
+ * on the whole line, bit for bit. */
+typedef int32_t (*tt_halo_fn)(void* user, int32_t gen, void* stream);
+typedef struct tt_slab {
+  int64_t dom_base;        /* global index of the context's first domain       */
+  int32_t has_prev;        /* 1: a slab lies before this one (m0 - 1 exists)   */
+  int32_t has_next;        /* 1: a slab lies after this one                    */
+  float* send_first;       /* [n_t0][D] device, caller-owned: the bests of the */
+  float* send_last;        /* slab's first / last m0 row, written by the       */
+                           /* library on `stream` before each exchange call    */
+  const float* recv_prev;  /* [n_t0][D] device: the previous slab's last row  */
+  const float* recv_next;  /* [n_t0][D] device: the next slab's first row     */
+  tt_halo_fn exchange;     /* called on the host at every exchange generation;*/
+                           /* a non-zero return aborts the search             */
+  void* user;              /* passed to exchange                              */
+} tt_slab;
+
+/* The search of tt_search on one slab (see tt_slab): same loop, draws keyed
+ * by dom_base + domain, the exchange's edge rows taken from recv_prev /
+ * recv_next. Runs eagerly (no graph: the exchange calls back to the host).
+ * *n_evals counts this slab's calls, imports from the neighbouring slabs
+ * included. Errors: INVALID_ARG (no grid, NULL slab or rows, dom_base out
+ * of range, exchange missing while a neighbour exists and exch_every > 0,
+ * or a non-zero return of exchange), CUDA. */
+tt_status tt_search_slab(tt_ctx* ctx, const tt_slab* slab, float* best_theta, float* best_S,
+                         uint64_t* n_evals, void* stream);
+
 /* Allocation-free semblance evaluation. The paper has no counterpart: this
  * entry point serves callers that cannot allocate device memory, such as a
  * plug-in whose host application owns every device buffer, or a service loop

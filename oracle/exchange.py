@@ -26,8 +26,13 @@ import numpy as np
 from .de import best_index, rank_key
 
 
-def neighbours(d: int, n_m0: int, n_t0: int):
-    """Present neighbours of domain d in the fixed order (t-1, t+1, m-1, m+1)."""
+def neighbours(d: int, n_m0: int, n_t0: int, has_prev: bool = False, has_next: bool = False):
+    """Present neighbours of domain d in the fixed order (t-1, t+1, m-1, m+1).
+
+    When the grid is one slab of a longer line, the m0 rows just before and
+    after it belong to the neighbouring slabs: with has_prev (has_next) the
+    neighbour (m-1) of the first row ((m+1) of the last row) is present and
+    returned as ("prev", it) (("next", it)), its best coming from that slab."""
     im, it = divmod(d, n_t0)
     out = []
     if it > 0:
@@ -36,8 +41,12 @@ def neighbours(d: int, n_m0: int, n_t0: int):
         out.append(d + 1)
     if im > 0:
         out.append(d - n_t0)
+    elif has_prev:
+        out.append(("prev", it))
     if im < n_m0 - 1:
         out.append(d + n_t0)
+    elif has_next:
+        out.append(("next", it))
     return out
 
 
@@ -49,16 +58,21 @@ def worst_slots(fit, exclude: int, n: int):
     return order[:n]
 
 
-def exchange_plan(n_m0, n_t0, pop, fit, best_theta):
-    """imports [n_dom, 4, D] (zeros where absent) and slots [n_dom, 4] (-1 absent)."""
+def exchange_plan(n_m0, n_t0, pop, fit, best_theta, halo_prev=None, halo_next=None):
+    """imports [n_dom, 4, D] (zeros where absent) and slots [n_dom, 4] (-1
+    absent). halo_prev / halo_next [n_t0, D], if given, are the snapshot
+    bests of the m0 rows just before / after the grid (neighbouring slabs)."""
     n_dom, NP, D = pop.shape
     imports = np.zeros((n_dom, 4, D), np.float32)
     slots = np.full((n_dom, 4), -1, np.int32)
     for d in range(n_dom):
-        nb = neighbours(d, n_m0, n_t0)
+        nb = neighbours(d, n_m0, n_t0, halo_prev is not None, halo_next is not None)
         ws = worst_slots(fit[d], best_index(fit[d]), len(nb))
         for q, (e, s) in enumerate(zip(nb, ws)):
-            imports[d, q] = best_theta[e]
+            if isinstance(e, tuple):
+                imports[d, q] = (halo_prev if e[0] == "prev" else halo_next)[e[1]]
+            else:
+                imports[d, q] = best_theta[e]
             slots[d, q] = s
     return imports, slots
 

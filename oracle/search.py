@@ -55,17 +55,28 @@ def polish_point(x, dt, dm, h, t0, op, w, theta0, lo, hi, steps, lr):
     return best_th, best_S, steps + 1
 
 
-def search(traces, mid, off, prob, cfg, *, history=None, jade_states=None):
+def search(traces, mid, off, prob, cfg, *, history=None, jade_states=None, dom_base=0,
+           halo=None):
     """Run the search over every domain of ``prob`` with settings ``cfg``
     (attributes np, ng, F, CR, seed, lo, hi, exch_every, polish_steps,
     polish_lr and optionally adapt). ``history``, if a list, receives the
     mean best S per gen; ``jade_states``, if a list, the final adaptation
-    state of every domain."""
+    state of every domain.
+
+    One slab of a longer line: ``dom_base`` is the global index of the
+    grid's first domain (it keys the random numbers, so a slab draws what
+    the whole-line search draws for the same domains), and ``halo``, if
+    given, is called at every exchange as halo(g, first_row, last_row) with
+    the snapshot bests of the slab's first and last m0 rows [n_t0, D]; it
+    returns the bests of the neighbouring slabs' adjacent rows (prev_row,
+    next_row), None where the slab is at a line end."""
     lo = np.asarray(cfg.lo, np.float32)
     hi = np.asarray(cfg.hi, np.float32)
     n_dom, NP, D = prob.n_dom, cfg.np, len(cfg.lo)
+    gdoms = range(dom_base, dom_base + n_dom)
     pop = np.zeros((n_dom, NP, D), np.float32)
-    pop, _, _, _ = de_mod.de_step(0, pop, None, None, None, cfg.seed, cfg.F, cfg.CR, lo, hi)
+    pop, _, _, _ = de_mod.de_step(0, pop, None, None, None, cfg.seed, cfg.F, cfg.CR, lo, hi,
+                                  domains=gdoms)
     fit = _eval(traces, mid, off, prob, pop)
     n_evals = n_dom * NP
     grid = cfg.exch_every > 0 and prob.n_m0 * prob.n_t0 == n_dom and n_dom > 0
@@ -75,22 +86,26 @@ def search(traces, mid, off, prob, cfg, *, history=None, jade_states=None):
         if adapt:
             trial = np.empty_like(pop)
             for d in range(n_dom):
-                trial[d], _ = jade.trial_population(states[d], cfg.seed, d, g, pop[d], fit[d],
-                                                    lo, hi)
+                trial[d], _ = jade.trial_population(states[d], cfg.seed, dom_base + d, g,
+                                                    pop[d], fit[d], lo, hi)
         else:
             pop, fit, trial, _ = de_mod.de_step(g, pop, fit, None, None, cfg.seed, cfg.F,
-                                                cfg.CR, lo, hi)
+                                                cfg.CR, lo, hi, domains=gdoms)
         tfit = _eval(traces, mid, off, prob, trial)
         n_evals += n_dom * NP
         for d in range(n_dom):
             if adapt:
-                pop[d], fit[d] = jade.select_adapt(states[d], cfg.seed, d, g, pop[d], fit[d],
-                                                   trial[d], tfit[d])
+                pop[d], fit[d] = jade.select_adapt(states[d], cfg.seed, dom_base + d, g, pop[d],
+                                                   fit[d], trial[d], tfit[d])
             else:
                 pop[d], fit[d] = de_mod.select(pop[d], fit[d], trial[d], tfit[d])
         if grid and g % cfg.exch_every == 0:
             snap = ex.best_snapshot(pop, fit)
-            imports, slots = ex.exchange_plan(prob.n_m0, prob.n_t0, pop, fit, snap)
+            prev_row = next_row = None
+            if halo is not None:
+                prev_row, next_row = halo(g, snap[:prob.n_t0].copy(), snap[-prob.n_t0:].copy())
+            imports, slots = ex.exchange_plan(prob.n_m0, prob.n_t0, pop, fit, snap,
+                                              prev_row, next_row)
             ifit = _eval(traces, mid, off, prob, imports)
             ifit[slots < 0] = 0.0
             n_evals += int(np.sum(slots >= 0))

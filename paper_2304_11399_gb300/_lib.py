@@ -59,6 +59,15 @@ class Stats(C.Structure):
                 ("timed_launches", C.c_uint64)]
 
 
+HaloFn = C.CFUNCTYPE(I32, P, I32, P)
+
+
+class Slab(C.Structure):
+    _fields_ = [("dom_base", C.c_int64), ("has_prev", I32), ("has_next", I32),
+                ("send_first", P), ("send_last", P), ("recv_prev", P), ("recv_next", P),
+                ("exchange", HaloFn), ("user", P)]
+
+
 SIGNATURES = {
     "tt_last_error": (C.c_char_p, [P]),
     "tt_version": (C.c_char_p, []),
@@ -75,6 +84,7 @@ SIGNATURES = {
     "tt_neighbor_exchange": (I32, [P, I32, I32, P, P, P, P, P, P]),
     "tt_polish": (I32, [P, P, P, I32, C.c_float, P]),
     "tt_search": (I32, [P, P, P, C.POINTER(C.c_uint64), P]),
+    "tt_search_slab": (I32, [P, C.POINTER(Slab), P, P, C.POINTER(C.c_uint64), P]),
     "tt_ctx_profile": (I32, [P, I32]),
     "tt_ctx_stats": (I32, [P, C.POINTER(Stats), I32]),
     "tt_semblance_eval_noalloc": (I32, [C.POINTER(Gathers), C.POINTER(ProblemT), P, I32, P, P]),

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_de_step(const DeArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d = blockIdx.x * kWarps + warp;
   if (d >= a.n_dom) return;  // uniform per warp
-  const int gd = a.dom_map ? a.dom_map[d] : d;  // global id: the Philox key's domain
+  const int gd = a.dom_map ? a.dom_map[d] : a.dom_base + d;  // the Philox key's domain
   if (gd < 0) return;
   const int NP = a.NP, D = a.D;
   float* gpop = a.pop + (size_t)d * NP * D;
@@ -300,19 +300,25 @@ __global__ void __launch_bounds__(kWarps * 32)
 // q-th worst member by (fitness ascending, index ascending), the domain's
 // own best excluded. Reads the best snapshot only; writes pop, imports and
 // slots (the imports' fitness is written by the scatter-mode semblance).
+// On a slab of a sharded line, the (m0-1) neighbour of the first row and the
+// (m0+1) neighbour of the last row are rows of the neighbouring slabs, read
+// from halo_prev / halo_next [n_t0][D] when given.
 __global__ void __launch_bounds__(kWarps * 32)
     k_exchange_plan(int n_m0, int n_t0, int NP, int D, const float* best_theta, float* pop,
-                    const float* fit, float* imports, int* slots) {
+                    const float* fit, float* imports, int* slots, const float* halo_prev,
+                    const float* halo_next) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d = blockIdx.x * kWarps + warp;
   if (d >= n_m0 * n_t0) return;
   const int im = d / n_t0, it = d - im * n_t0;
-  int nb[4];
+  const float* nb[4];  // the neighbours' bests, in the order (t-1, t+1, m-1, m+1)
   int nn = 0;
-  if (it > 0) nb[nn++] = d - 1;
-  if (it < n_t0 - 1) nb[nn++] = d + 1;
-  if (im > 0) nb[nn++] = d - n_t0;
-  if (im < n_m0 - 1) nb[nn++] = d + n_t0;
+  if (it > 0) nb[nn++] = best_theta + (size_t)(d - 1) * D;
+  if (it < n_t0 - 1) nb[nn++] = best_theta + (size_t)(d + 1) * D;
+  if (im > 0) nb[nn++] = best_theta + (size_t)(d - n_t0) * D;
+  else if (halo_prev) nb[nn++] = halo_prev + (size_t)it * D;
+  if (im < n_m0 - 1) nb[nn++] = best_theta + (size_t)(d + n_t0) * D;
+  else if (halo_next) nb[nn++] = halo_next + (size_t)it * D;
   const float* f = fit + (size_t)d * NP;
   const int own = warp_argmax(f, NP, lane);
   int chosen[4] = {-1, -1, -1, -1};
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int q = t / D, k = t - q * D;
     float v = 0.f;
     if (q < nn) {
-      v = best_theta[(size_t)nb[q] * D + k];
+      v = nb[q][k];
       pop[((size_t)d * NP + chosen[q]) * D + k] = v;
     }
     if (imports) imports[((size_t)d * 4 + q) * D + k] = v;
@@ -396,12 +402,12 @@ cudaError_t launch_best_snapshot(int n_dom, int NP, int D, const float* pop, con
 
 cudaError_t launch_exchange_plan(int n_m0, int n_t0, int NP, int D, const float* best_theta,
                                  float* pop, const float* fit, float* imports, int* slots,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const float* halo_prev,
+                                 const float* halo_next) {
   const int n = n_m0 * n_t0;
   if (n == 0) return cudaSuccess;
-  k_exchange_plan<<<(n + kWarps - 1) / kWarps, kWarps * 32, 0, s>>>(n_m0, n_t0, NP, D,
-                                                                    best_theta, pop, fit,
-                                                                    imports, slots);
+  k_exchange_plan<<<(n + kWarps - 1) / kWarps, kWarps * 32, 0, s>>>(
+      n_m0, n_t0, NP, D, best_theta, pop, fit, imports, slots, halo_prev, halo_next);
   return cudaGetLastError();
 }
 

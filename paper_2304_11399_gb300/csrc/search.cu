@@ -66,15 +66,21 @@ extern "C" tt_status tt_polish(tt_ctx* c, float* theta, float* S, int32_t steps,
 namespace {
 
 // Enqueue the whole search on `s`, writing the result to (best_theta, best_S).
+// `slab` (may be NULL) makes it one slab of a sharded line.
 tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t s,
-                      unsigned long long* n_evals) {
+                      unsigned long long* n_evals, const tt_slab* slab = nullptr) {
   const tt_de_cfg& cfg = c->cfg;
   const int NP = cfg.np, NG = cfg.ng;
   const bool grid = cfg.exch_every > 0 && c->n_m0 > 0 && c->n_t0 > 0 &&
                     (long long)c->n_m0 * c->n_t0 == c->n_dom;
+  const int base = slab ? int(slab->dom_base) : 0;
+  const bool prev = slab && slab->has_prev, next = slab && slab->has_next;
+  // imports per exchange: the grid's inner edges both ways, plus one per
+  // domain of an edge row with a neighbouring slab
   const unsigned long long edges =
       grid ? 2ull * ((unsigned long long)c->n_m0 * (c->n_t0 - 1) +
-                     (unsigned long long)c->n_t0 * (c->n_m0 - 1))
+                     (unsigned long long)c->n_t0 * (c->n_m0 - 1)) +
+                 (unsigned long long)c->n_t0 * ((prev ? 1 : 0) + (next ? 1 : 0))
            : 0ull;
   unsigned long long evals = 0;
   tt_status st = TT_OK;
@@ -83,8 +89,13 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
     st = tt_cuda_check(c, (expr), what);                         \
     if (st != TT_OK) return st;                                  \
   } while (0)
+  auto de_args = [&](int gen) {
+    tt::DeArgs d = tt_make_de_args(c, gen);
+    d.dom_base = base;
+    return d;
+  };
   // generation 0: initialise and evaluate
-  tt::DeArgs a = tt_make_de_args(c, 0);
+  tt::DeArgs a = de_args(0);
   a.pop = c->pop;
   a.fit = c->fit;
   STEP(c->counted(tt::launch_de_step(a, s)), "init");
@@ -93,7 +104,7 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
   int cur = 0;            // trial buffer written by the next mutation
   bool pending = false;   // trial[cur ^ 1] awaits selection
   for (int g = 1; g <= NG; ++g) {
-    a = tt_make_de_args(c, g);
+    a = de_args(g);
     a.pop = c->pop;
     a.fit = c->fit;
     a.trial = pending ? c->trial[cur ^ 1] : nullptr;
@@ -105,7 +116,7 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
     pending = true;
     cur ^= 1;
     if (grid && g % cfg.exch_every == 0) {
-      a = tt_make_de_args(c, g);
+      a = de_args(g);
       a.sel_gen = g;  // select-only: the trial of this generation
       a.pop = c->pop;
       a.fit = c->fit;
@@ -116,8 +127,21 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
       STEP(c->counted(tt::launch_best_snapshot(c->n_dom, NP, c->D, c->pop, c->fit, c->snap,
                                                 nullptr, s)),
            "snapshot");
+      if (prev || next) {
+        // the edge rows out, the neighbouring slabs' rows in
+        const size_t row = size_t(c->n_t0) * c->D * sizeof(float);
+        STEP(cudaMemcpyAsync(slab->send_first, c->snap, row, cudaMemcpyDeviceToDevice, s),
+             "send first row");
+        STEP(cudaMemcpyAsync(slab->send_last, c->snap + size_t(c->n_m0 - 1) * c->n_t0 * c->D,
+                             row, cudaMemcpyDeviceToDevice, s),
+             "send last row");
+        if (slab->exchange(slab->user, g, s) != 0)
+          return tt_fail(c, TT_ERR_INVALID_ARG, "slab exchange callback failed at gen %d", g);
+      }
       STEP(c->counted(tt::launch_exchange_plan(c->n_m0, c->n_t0, NP, c->D, c->snap, c->pop,
-                                               c->fit, c->imports, c->slots, s)),
+                                               c->fit, c->imports, c->slots, s,
+                                               prev ? slab->recv_prev : nullptr,
+                                               next ? slab->recv_next : nullptr)),
            "exchange");
       tt::EvalArgs ea = c->eval_args(c->imports, 4, c->fit);
       ea.slots = c->slots;
@@ -127,7 +151,7 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
     }
   }
   if (pending) {
-    a = tt_make_de_args(c, NG + 1);
+    a = de_args(NG + 1);
     a.sel_gen = NG;  // select-only: the last trial
     a.pop = c->pop;
     a.fit = c->fit;
@@ -206,4 +230,25 @@ extern "C" tt_status tt_search(tt_ctx* c, float* best_theta, float* best_S, uint
   c->trace_evals += c->g_trace_evals;
   if (n_evals) *n_evals = c->g_evals;
   return TT_OK;
+}
+
+extern "C" tt_status tt_search_slab(tt_ctx* c, const tt_slab* slab, float* best_theta,
+                                    float* best_S, uint64_t* n_evals, void* stream) {
+  if (!c) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->has_cfg) return tt_fail(c, TT_ERR_INVALID_ARG, "context was created without a cfg");
+  if (!slab) return tt_fail(c, TT_ERR_INVALID_ARG, "slab is NULL");
+  if (c->n_m0 <= 0 || c->n_t0 <= 0 || (long long)c->n_m0 * c->n_t0 != c->n_dom)
+    return tt_fail(c, TT_ERR_INVALID_ARG, "a slab needs the (m0, t0) grid of its domains");
+  if (slab->dom_base < 0 || slab->dom_base + c->n_dom > 0x7fffffffll)
+    return tt_fail(c, TT_ERR_INVALID_ARG, "dom_base out of range");
+  const bool edges = c->cfg.exch_every > 0 && (slab->has_prev || slab->has_next);
+  if (edges && (!slab->exchange || !slab->send_first || !slab->send_last ||
+                (slab->has_prev && !slab->recv_prev) || (slab->has_next && !slab->recv_next)))
+    return tt_fail(c, TT_ERR_INVALID_ARG, "a slab with neighbours needs exchange and its rows");
+  if (!best_theta || !best_S) return tt_fail(c, TT_ERR_INVALID_ARG, "NULL output array");
+  unsigned long long evals = 0;
+  tt_status st = search_body(c, best_theta, best_S, static_cast<cudaStream_t>(stream), &evals,
+                             slab);
+  if (st == TT_OK && n_evals) *n_evals = evals;
+  return st;
 }

@@ -78,6 +78,7 @@ cudaError_t launch_stack(const EvalArgs& a, float* out, cudaStream_t s);
 struct DeArgs {
   int n_dom, NP, D, gen;
   const int* dom_map;       // optional: local domain -> global id keying Philox (-1: skip)
+  int dom_base;             // without a map: global id = dom_base + local domain
   float* pop;
   float* fit;
   const float* trial;
@@ -166,9 +167,12 @@ __device__ inline int warp_argmax(const float* fit, int NP, int lane) {
 }
 cudaError_t launch_best_snapshot(int n_dom, int NP, int D, const float* pop, const float* fit,
                                  float* best_theta, float* best_S, cudaStream_t s);
+// halo_prev / halo_next [n_t0][D] (may be NULL): bests of the m0 rows just
+// before / after the grid, held by the neighbouring slabs of a sharded line
 cudaError_t launch_exchange_plan(int n_m0, int n_t0, int NP, int D, const float* best_theta,
                                  float* pop, const float* fit, float* imports, int* slots,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const float* halo_prev = nullptr,
+                                 const float* halo_next = nullptr);
 cudaError_t launch_polish_update(int n_dom, int D, float* th, const float* g, const float* S,
                                  float* best_th, float* best_S, const float* lo, const float* hi,
                                  float lr, int first, int last, cudaStream_t s);

@@ -262,6 +262,43 @@ def tt_search(ctx: Context, best_theta=None, best_S=None, stream=None):
     return best_theta, best_S, int(n.value)
 
 
+def tt_search_slab(ctx: Context, dom_base: int, has_prev: bool, has_next: bool, exchange=None,
+                   best_theta=None, best_S=None, stream=None):
+    """The search on one slab of a sharded line (see include/tt.h, tt_slab).
+    ``exchange(gen, send_first, send_last, recv_prev, recv_next)`` receives
+    four [n_t0, D] device tensors: it sends the first two to the previous and
+    next slab and fills the last two with theirs (e.g.
+    ``slab.halo_exchange``). Returns (best_theta, best_S, n_evals)."""
+    if best_theta is None:
+        best_theta = torch.empty((ctx.n_dom, ctx.D), dtype=torch.float32, device=ctx.device)
+    if best_S is None:
+        best_S = torch.empty((ctx.n_dom,), dtype=torch.float32, device=ctx.device)
+    rows = [torch.zeros((ctx.n_t0, ctx.D), dtype=torch.float32, device=ctx.device)
+            for _ in range(4)]
+    failure = []
+
+    def trampoline(user, gen, stream_ptr):
+        try:
+            exchange(int(gen), *rows)
+            return 0
+        except BaseException as e:  # re-raised below, after the library returns
+            failure.append(e)
+            return 1
+
+    fn = L.HaloFn(trampoline) if exchange is not None else L.HaloFn()
+    sl = L.Slab(int(dom_base), 1 if has_prev else 0, 1 if has_next else 0,
+                *(C.c_void_p(t.data_ptr()) for t in rows), fn, None)
+    n = C.c_uint64(0)
+    st = ctx.lib.tt_search_slab(ctx.handle, C.byref(sl),
+                                _ptr(best_theta, "best_theta", shape=(ctx.n_dom, ctx.D)),
+                                _ptr(best_S, "best_S", shape=(ctx.n_dom,)), C.byref(n),
+                                _stream(stream))
+    if failure:
+        raise failure[0]
+    _check(ctx.lib, ctx.handle, st)
+    return best_theta, best_S, int(n.value)
+
+
 def tt_ens_search(ctx: Context, np_f: int = 5, ng_f: int = 1, np_bf: int = 5, ng_bf: int = 1,
                   n_skip: int = 2, n_cycle: int = 1, n_bucket: int = 64, best_theta=None,
                   best_S=None, stream=None):

@@ -7,7 +7,8 @@ domains and their apertures. It evaluates no coherence, runs no search and
 draws none of the random numbers the search itself uses.
 """
 from .gathers import (  # noqa: F401
-    Line, Problem, make_line, cmp_problem, line_problem, batched_problems,
+    Line, Problem, make_line, cmp_problem, line_problem, batched_problems, slab_bounds,
+    slab_problem,
     crs_recentre, CMP, CRS,
 )
 from . import configs  # noqa: F401

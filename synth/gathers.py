@@ -196,6 +196,34 @@ def line_problem(line: Line, *, half_window: int, ap_half: int, cmps=None,
                    n_m0=G, n_t0=int(t0s.size))
 
 
+def slab_bounds(n_m0: int, world: int, rank: int):
+    """CMPs [c0, c1) of slab ``rank`` when n_m0 CMPs are cut into ``world``
+    contiguous slabs whose sizes differ by at most one (the first
+    n_m0 % world slabs take the extra CMP)."""
+    base, extra = divmod(n_m0, world)
+    c0 = rank * base + min(rank, extra)
+    return c0, c0 + base + (1 if rank < extra else 0)
+
+
+def slab_problem(line: Line, c0: int, c1: int, *, half_window: int, ap_half: int):
+    """The inputs of one slab of a sharded line search: the CRS problem of
+    CMPs [c0, c1) (every sample a domain, m0-major) over a copy of only the
+    traces its apertures read -- the slab's own CMPs plus a read-only halo
+    of ap_half CMPs on each side, clipped at the line ends -- with the
+    aperture lists re-indexed into that copy (same traces, same order).
+    Returns (traces, mid, off, problem, dom_base, has_prev, has_next):
+    dom_base is the global index of the slab's first domain on the whole
+    line's m0-major grid; has_prev / has_next say whether CMPs exist before
+    c0 / from c1 on."""
+    prob = line_problem(line, half_window=half_window, ap_half=ap_half,
+                        cmps=list(range(c0, c1)))
+    h0 = max(0, c0 - ap_half) * line.n_off
+    h1 = min(line.n_cmp, c1 + ap_half) * line.n_off
+    prob.ap_idx = (prob.ap_idx - h0).astype(np.int32)
+    return (np.ascontiguousarray(line.traces[h0:h1]), line.mid[h0:h1].copy(),
+            line.off[h0:h1].copy(), prob, c0 * line.ns, c0 > 0, c1 < line.n_cmp)
+
+
 def batched_problems(*, n_prob: int, ntr_range, ns_range, dts, seed: int,
                      n_events: int = 8, snr: float = 5.0, ap_cmp: int = 10,
                      dcmp: float = 12.5, doff: float = 50.0, max_off: float = 2350.0,

@@ -1,6 +1,6 @@
 """The benchmark's multi-rank logic on CPU: two gloo ranks (world size 2)
-reduce their step times to the maximum, compute the whole-job value, and only
-rank 0 of the reference arm prints."""
+reduce their step times to the maximum, sum their domain counts, compute the
+whole-job value, and only rank 0 of the reference arm prints."""
 import json
 import os
 import socket
@@ -30,7 +30,7 @@ def _worker(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     w, r, lr = bench.rank_env()
     t = bench.max_over_ranks(1.5 + rank, w)
-    out[rank] = (w, r, lr, t, bench.job_value(300, w, t))
+    out[rank] = (w, r, lr, t, bench.job_value(300, w, t), bench.sum_over_ranks(10 + rank, w))
     dist.destroy_process_group()
 
 
@@ -39,10 +39,11 @@ def test_two_gloo_ranks_reduce_to_the_slowest():
     out = mp.Manager().dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     for rank in range(world):
-        w, r, lr, t, v = out[rank]
+        w, r, lr, t, v, n = out[rank]
         assert (w, r, lr) == (2, rank, rank)
         assert t == 2.5                      # max over ranks
         assert v == pytest.approx(2 * 300 / 2.5)
+        assert n == 21                       # sum over ranks (slab domain counts)
 
 
 def test_reference_arm_prints_on_rank_zero_only():
