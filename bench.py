@@ -302,6 +302,38 @@ def _autotune(tt, ctx, n_dom, np_, D, dev):
     return tuned, f"{tt.tt_ctx_get_option(ctx, 'kernel')}/{tt.tt_ctx_get_option(ctx, 'block')}"
 
 
+def ens_compare(tt, wl, dev, stream):
+    """The ENS sweep (tt_ens_search, Sec. 3.3-3.6) on the same line at the
+    paper's cheapest setting, NP_f 5 x NG_f 1, NP_bf 5 x NG_bf 1, N_skip 2,
+    N_cycle 1, buckets of 64 traces: one graph-capturing run, then the median
+    of five timed replays, with the call count, the RMS of the semblance
+    panel and the recovery of the event-centred parameters."""
+    import copy
+    import torch
+    de = copy.copy(wl.de)
+    de.np, de.ng, de.exch_every, de.polish_steps = 5, 1, 0, 0
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, wl.problem, de, device=dev)
+    tt.tt_ens_search(ctx, 5, 1, 5, 1, 2, 1, 64)
+    ts = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        th, S, n = tt.tt_ens_search(ctx, 5, 1, 5, 1, 2, 1, 64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    secs = float(np.median(ts))
+    S = S.cpu().numpy().astype(np.float64)
+    out = {"setting": "NP 5 x NG 1 both ways, N_skip 2, N_cycle 1, buckets of 64 traces",
+           "seconds": secs, "value": wl.problem.n_dom / secs,
+           "calls_per_sample": n / wl.problem.n_dom,
+           "rms_coherence": float(np.sqrt(np.mean(S * S))),
+           "recovery": recovery(wl, th.cpu().numpy())}
+    ctx.close()
+    return out
+
+
 def large_slab_compare(tt, dev, stream, n_slab=100, sample_frac=0.01):
     """The large line (2000 CMPs x 120 offsets x 2000 samples at 2 ms, 60
     events, SNR 2, aperture +-25 CMPs, DE 96 x 120 with exchange and polish):
@@ -798,6 +830,7 @@ def main():
         one_form("bf16_stored", "bf16", "packed", wl.de.polish_steps,
                  "BF16 trace copy, FP32 arithmetic, FP64 chunked energy, polish")
         comparison["speedup_vs_plain_fp32"] = value / comparison["plain_fp32"]["value"]
+        comparison["ens_sweep"] = ens_compare(tt, wl, dev, stream)
         if not args.no_large:
             comparison["large_line_slab"] = large_slab_compare(tt, dev, stream)
         if not args.no_batched:
