@@ -51,7 +51,7 @@ cudaError_t launch(const EvalArgs& a, cudaStream_t s, bool grad) {
     if (a.split_part && a.split_ticket) {
       if (units <= (long long)a.n_sm * kSplitSmallPerSm) {
         S = sk::kSplitMultiWarps;
-        b.split_blocks = kSplitMaxBlocks;
+        b.split_blocks = units * 2 <= a.n_sm ? kSplitTinyBlocks : kSplitSmallBlocks;
       } else if (units < (long long)a.n_sm * kSplitMultiPerSm) {
         S = 8;
         b.split_blocks = 2;

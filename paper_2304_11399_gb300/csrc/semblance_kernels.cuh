@@ -398,9 +398,9 @@ __device__ __forceinline__ void eval_unit(const EvalArgs& a, long long unit, int
 // shared memory and are added in slice order; with B > 1 each block writes
 // its sums to global scratch and the last block of the unit to arrive (an
 // atomic ticket, no waiting) adds the B block sums in block order. (S, B)
-// is (16, 4) up to 2 units per SM, (8, 2) below 12 per SM and (8, 1) above
-// (304 and 1824 units on a 152-SM device), so that
-// the GPU stays busy. The summation order depends on (S, B) and
+// is (8, 9) up to half a unit per SM, (8, 7) up to 2 units per SM, (8, 2)
+// below 12 per SM and (8, 1) above (76, 304 and 1824 units on a 152-SM
+// device), so that the GPU stays busy. The summation order depends on (S, B) and
 // differs from the one-warp-per-unit kernel, so all are chosen by launch
 // size alone -- every variant of a launch runs the same code -- and results
 // stay reproducible.
@@ -413,14 +413,17 @@ inline int split_warps(long long units, int n_sm) {
 }
 
 // Launches of at most n_sm * kSplitSmallPerSm units run kSplitMultiWarps warps per
-// block and kSplitMaxBlocks blocks per unit: 64 slices per aperture in
-// 512-thread blocks, two of which share an SM, so one block's barrier overlaps
-// the other's loads. The best of the (S, B) pairs timed on ENS sweeps
-// (S x B = 64 with 512- or 256-thread blocks; 1024-thread blocks were 12-20%
-// slower). Below n_sm * kSplitMultiPerSm units, (8, 2): timed 17% faster than
-// (8, 1) on the 938-unit launches of an ENS 30 x 30 sweep, while from about
-// 2500 units (ENS 80 x 80) one block per unit is best.
-constexpr int kSplitMultiWarps = 16;
+// block, kSplitSmallBlocks blocks per unit (56 slices per aperture), or
+// kSplitTinyBlocks (72 slices) up to n_sm / 2 units: 256-thread blocks, four
+// of which share an SM, so that one block's barrier overlaps the others'
+// loads. The best of the (S, B) pairs timed on the ENS 5 x 1 sweep, whose
+// launches hold 157 and 63 units (21.7 ms against 23.1 for (16, 4); (8, 5),
+// (8, 6), (8, 8), (16, 3), (16, 5) and for the smaller launches (8, 6),
+// (16, 4), (16, 8) were slower). Below n_sm * kSplitMultiPerSm units, (8, 2):
+// timed 17% faster than (8, 1) on the 938-unit launches of an ENS 30 x 30
+// sweep, while from about 2500 units (ENS 80 x 80) one block per unit is
+// best.
+constexpr int kSplitMultiWarps = 8;
 
 // dynamic shared memory of a split block: FP64 energies [S][64], FP32
 // energies [S][64], stack sums [S][64][K]

@@ -20,18 +20,23 @@ constexpr int op_dim(int op) { return op == TT_OP_CMP ? 1 : op == TT_OP_CRS ? 3 
 // fewer than n_sm * kSplitUnitsPerSm units (one warp per unit then leaves
 // SMs short of their 32 resident warps) splits each unit's aperture over
 // the warps of a block; up to n_sm * kSplitSmallPerSm units a unit spreads
-// over kSplitMaxBlocks blocks, below n_sm * kSplitMultiPerSm over two. The
-// multi-block launches combine partial sums in context scratch.
+// over kSplitSmallBlocks blocks (kSplitTinyBlocks up to n_sm / 2 units),
+// below n_sm * kSplitMultiPerSm over two. The multi-block launches combine
+// partial sums in context scratch: one set per (unit, block), so the scratch
+// holds the largest units x blocks of any launch, at most
+// max(2 kSplitMultiPerSm, kSplitSmallPerSm kSplitSmallBlocks,
+// kSplitTinyBlocks / 2) n_sm sets.
 constexpr int kSplitUnitsPerSm = 32;
 constexpr int kSplitSmallPerSm = 2;
 constexpr int kSplitMultiPerSm = 12;
-constexpr int kSplitMaxBlocks = 4;
+constexpr int kSplitSmallBlocks = 7;
+constexpr int kSplitTinyBlocks = 9;
+static_assert(kSplitSmallPerSm * kSplitSmallBlocks <= 2 * kSplitMultiPerSm &&
+                  kSplitTinyBlocks <= 4 * kSplitMultiPerSm,
+              "every split shape fits the 2 kSplitMultiPerSm n_sm part sets");
 // scratch sets (one per block of a multi-block split launch) and tickets
 // (one per unit) for a device of n_sm SMs
-inline long long split_part_sets(int n_sm) {
-  const long long a = 2ll * kSplitMultiPerSm, b = (long long)kSplitSmallPerSm * kSplitMaxBlocks;
-  return (a > b ? a : b) * n_sm;
-}
+inline long long split_part_sets(int n_sm) { return 2ll * kSplitMultiPerSm * n_sm; }
 inline long long split_tickets(int n_sm) { return (long long)kSplitMultiPerSm * n_sm; }
 constexpr int kSplitPartStride = 2 * 8 + 2;  // floats per pair: K + 1 for the widest window
 

@@ -53,9 +53,10 @@ def batch():
 
 @pytest.mark.parametrize("P", [1, 4, 20, 64, 130])
 def test_variants_bit_identical_on_a_line(P):
-    """2400 domains: P = 1 and 4 split the aperture over 4 blocks of 16
-    warps per unit, P = 20 (750 units) over 2 blocks of 8 warps, P = 64
-    (2400 units) over one block of 8 warps,
+    """2400 domains: P = 1 (38 units) splits the aperture over 9 blocks of 8
+    warps per unit, P = 4 (150 units) over 7 blocks of 8 warps, P = 20 (750
+    units) over 2 blocks of 8 warps, P = 64 (2400 units) over one block of 8
+    warps,
     P = 130 (4875 units) is too large to split; the oracle checks a sample
     of domains for the two largest P."""
     wl = small_line(31)
