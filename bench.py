@@ -636,6 +636,29 @@ def roofline(tt, ctx, prob, stats, args, clk):
     return roof
 
 
+def l1_probe(tt, ctx, stream, roof):
+    """The L1 load bandwidth measured by the library's probe (coalesced
+    4-byte loads from an L1-resident window, 32 warps per SM like K1), one
+    warm-up launch then five timed with CUDA events; beside the derived
+    peak, as bytes per clock per SM at the same clock, and K1's achieved
+    byte rate as a fraction of it."""
+    import torch
+    tt.tt_ctx_probe_l1(ctx, 200, stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    n = sum(tt.tt_ctx_probe_l1(ctx, 4000, stream) for _ in range(5))
+    b.record(stream)
+    torch.cuda.synchronize()
+    gbs = n / (a.elapsed_time(b) / 1e3) / 1e9
+    clk = roof["sm_count"] * roof["sm_max_mhz"] * 1e6
+    return {"gbs": gbs, "bytes_per_clk_per_sm": gbs * 1e9 / clk if clk else None,
+            "k1_frac_of_probe": roof["achieved"] / gbs,
+            "method": "tt_ctx_probe_l1: 8 blocks x 256 threads per SM, 32 coalesced 4-byte "
+                      "ld.global.nc per thread per iteration from a 16 KiB window, 5 x 4000 "
+                      "iterations, CUDA events; bytes per clock at the maximum SM clock"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -795,6 +818,7 @@ def main():
         roof["semblance_share_of_step"] = stats["semblance_ms"] / ms
         if rank == 0:
             roof["l2_probe"] = l2_probe(dev, stream)
+            roof["l1_probe"] = l1_probe(tt, ctx, stream, roof)
     # the same search in other forms on the same GPU (rank 0, line workload)
     comparison = None
     if rank == 0 and world == 1 and args.workload == "line" and not args.no_compare:

@@ -298,6 +298,18 @@ tt_status tt_ctx_profile(tt_ctx* ctx, int32_t enable);
  * launches are pending this waits for the last recorded event. */
 tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
 
+/* L1 load-bandwidth probe (no passage in the paper: a measurement aid for
+ * the semblance kernel's roofline). Enqueues on `stream` one kernel in which
+ * 8 blocks of 256 threads per SM each stream `iters` x 32 coalesced 4-byte
+ * loads per thread (32 consecutive floats per warp request, the load K1
+ * gathers its windows with) from a 16 KiB window of the context's scratch
+ * that stays in L1 (32 warps resident per SM, as the semblance kernel);
+ * *bytes (host) receives the bytes it loads. Time it with events on
+ * `stream`. It reads the scratch's contents, whatever they are, and may
+ * write one float of it (the scratch holds nothing between launches).
+ * Errors: INVALID_ARG for iters < 1 or a NULL bytes. */
+tt_status tt_ctx_probe_l1(tt_ctx* ctx, int32_t iters, double* bytes, void* stream);
+
 /* Launch options of a context (tt_ctx_set_option / tt_ctx_get_option):
  *  TT_OPT_KERNEL  semblance kernel variant for forward evaluations:
  *                 TT_KERNEL_PACKED (default; two parameter vectors per thread

@@ -87,6 +87,7 @@ SIGNATURES = {
     "tt_search_slab": (I32, [P, C.POINTER(Slab), P, P, C.POINTER(C.c_uint64), P]),
     "tt_ctx_profile": (I32, [P, I32]),
     "tt_ctx_stats": (I32, [P, C.POINTER(Stats), I32]),
+    "tt_ctx_probe_l1": (I32, [P, I32, C.POINTER(C.c_double), P]),
     "tt_semblance_eval_noalloc": (I32, [C.POINTER(Gathers), C.POINTER(ProblemT), P, I32, P, P]),
     "tt_ctx_set_option": (I32, [P, I32, C.c_int64]),
     "tt_ctx_get_option": (I32, [P, I32, C.POINTER(C.c_int64)]),

@@ -79,6 +79,8 @@ struct EvalArgs {
 cudaError_t launch_semblance(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_stack(const EvalArgs& a, float* out, cudaStream_t s);
+cudaError_t launch_l1_probe(const float* buf, float* out, int n_sm, int iters, double* bytes,
+                            cudaStream_t s);
 
 struct DeArgs {
   int n_dom, NP, D, gen;

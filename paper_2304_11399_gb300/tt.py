@@ -367,6 +367,15 @@ def tt_ctx_profile(ctx: Context, enable: bool = True):
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_profile(ctx.handle, 1 if enable else 0))
 
 
+def tt_ctx_probe_l1(ctx: Context, iters: int = 4000, stream=None) -> float:
+    """Enqueue the L1 load-bandwidth probe; returns the bytes it loads (time
+    it with CUDA events on the stream)."""
+    b = C.c_double(0.0)
+    _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_probe_l1(ctx.handle, int(iters), C.byref(b),
+                                                        _stream(stream)))
+    return b.value
+
+
 def tt_ctx_stats(ctx: Context, reset: bool = False) -> dict:
     """Launch counters and the summed device time of semblance launches."""
     st = L.Stats()

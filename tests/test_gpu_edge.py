@@ -78,3 +78,31 @@ def test_one_sample_records_and_one_trace_apertures(w):
     assert np.max(np.abs(S - ref)) <= 1e-5
     sref = oracle.stack.stack_many(x, mid, off, prob, theta[:, 0])
     assert np.max(np.abs(st - sref)) <= 1e-6
+
+
+def test_l1_probe_measures_a_plausible_rate():
+    """The L1 probe runs on the context's scratch, reports the bytes it
+    loads, and its rate lies below twice the derived data-path bound
+    (SMs x 128 B/clk at 2.1 GHz) and above a tenth of it."""
+    import torch
+    import paper_2304_11399_gb300 as tt
+    from gpu_util import dev, small_line
+    wl = small_line(3, n_cmp=4, ns=80, ap_half=1)
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, wl.problem, None, device=dev())
+    n_sm = tt.tt_ctx_get_option(ctx, "sm_count")
+    assert n_sm == torch.cuda.get_device_properties(dev()).multi_processor_count
+    assert tt.tt_ctx_get_option(ctx, "split_max_pairs") == n_sm * 32 * 64
+    tt.tt_ctx_probe_l1(ctx, 10)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    n = tt.tt_ctx_probe_l1(ctx, 500)
+    b.record()
+    torch.cuda.synchronize()
+    assert n == n_sm * 8 * 256 * 500 * 32 * 4
+    rate = n / (a.elapsed_time(b) / 1e3)
+    bound = n_sm * 128 * 2.1e9
+    assert 0.1 * bound < rate < 2.0 * bound, (rate, bound)
+    with pytest.raises(tt.TTError):
+        tt.tt_ctx_probe_l1(ctx, 0)
+    ctx.close()
