@@ -584,17 +584,20 @@ def device_counts(ctx_sm):
     return int(ctx_sm), mhz, src
 
 
-def roofline(tt, ctx, prob, stats, args, clk):
+def roofline(tt, ctx, prob, stats, args, clk, stream):
     """Roofline of K1 from the library's live CUDA-event timing of every
-    semblance launch in the timed steps. The headline bound is the on-chip
-    data path that K1's window loads go through: every (trace, vector) pair
-    gathers 2w + 2 samples (48 B in FP32, 24 B in BF16), and the L1 /
-    shared-memory data path moves 128 B per clock per SM, so
-      peak = n_sm x 128 B x max SM clock,
+    semblance launch in the timed steps. The bound is the on-chip data path
+    that K1's window loads go through: every (trace, vector) pair gathers
+    2w + 2 samples (48 B in FP32, 24 B in BF16) with 4-byte loads that hit
+    in L1, so
       achieved = pairs per launch x bytes per pair / mean launch time,
-    both printed with the SM count and clock they use. Beside it: the FP32
-    pipe (n_sm x 128 lanes x 2 flops x clock) under the two work counts, and
-    the DRAM bytes of one launch from an ncu capture (traffic)."""
+      peak = the L1 load rate the library's probe measures on this GPU with
+             the same load instruction (coalesced, one cache line per warp
+             request, every resident warp loading);
+    beside it the derived line rate, n_sm x 128 B x max SM clock, printed
+    with the SM count and clock it uses, the FP32 pipe (n_sm x 128 lanes x 2
+    flops x clock) under the two work counts, and the DRAM bytes of one
+    launch from an ncu capture (traffic)."""
     n_sm, mhz, mhz_src = device_counts(tt.tt_ctx_get_option(ctx, "sm_count"))
     if mhz is None:
         mhz = clk.get("sm_max_mhz") or 0.0
@@ -604,7 +607,9 @@ def roofline(tt, ctx, prob, stats, args, clk):
     pairs_launch = stats["trace_evals"] / stats["semblance_launches"]
     pairs_s = pairs_launch / (ms_launch / 1e3)
     achieved = pairs_s * bytes_pair / 1e9
-    peak = n_sm * L1_BYTES_PER_CLK * mhz * 1e6 / 1e9
+    derived = n_sm * L1_BYTES_PER_CLK * mhz * 1e6 / 1e9
+    probe = l1_probe(tt, ctx, stream, n_sm, mhz)
+    peak = probe["gbs"]
     kern = f"{tt.tt_ctx_get_option(ctx, 'kernel')}/{tt.tt_ctx_get_option(ctx, 'block')}"
     traffic = (K1_LINE_DRAM_BYTES if (args.workload == "line" and args.storage == "f32" and
                                       not args.cmps and kern == K1_LINE_DRAM_KERNEL) else None)
@@ -613,8 +618,11 @@ def roofline(tt, ctx, prob, stats, args, clk):
     roof = {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if peak else None, "traffic": traffic,
             "kernel": f"k_semblance ({kern})",
-            "peak_source": (f"derived: {n_sm} SMs (device query) x {L1_BYTES_PER_CLK} B/clk x "
-                            f"{mhz:.0f} MHz ({mhz_src})"),
+            "peak_source": "measured: " + probe["method"],
+            "l1_probe": probe,
+            "derived": {"peak": derived, "frac": achieved / derived if derived else None,
+                        "source": (f"{n_sm} SMs (device query) x {L1_BYTES_PER_CLK} B/clk x "
+                                   f"{mhz:.0f} MHz ({mhz_src})")},
             "sm_count": n_sm, "sm_max_mhz": mhz, "bytes_per_pair": bytes_pair,
             "pairs_per_launch": pairs_launch, "per_launch_ms": ms_launch,
             "trace_evals_per_s": pairs_s, "trace_samples_per_s": pairs_s * (2 * w + 1),
@@ -636,12 +644,11 @@ def roofline(tt, ctx, prob, stats, args, clk):
     return roof
 
 
-def l1_probe(tt, ctx, stream, roof):
+def l1_probe(tt, ctx, stream, n_sm, mhz):
     """The L1 load bandwidth measured by the library's probe (coalesced
-    4-byte loads from an L1-resident window, 32 warps per SM like K1), one
-    warm-up launch then five timed with CUDA events; beside the derived
-    peak, as bytes per clock per SM at the same clock, and K1's achieved
-    byte rate as a fraction of it."""
+    4-byte loads from an L1-resident window, one wave of resident blocks),
+    one warm-up launch then five timed with CUDA events, also as bytes per
+    clock per SM at the maximum SM clock."""
     import torch
     tt.tt_ctx_probe_l1(ctx, 200, stream)
     torch.cuda.synchronize()
@@ -651,12 +658,12 @@ def l1_probe(tt, ctx, stream, roof):
     b.record(stream)
     torch.cuda.synchronize()
     gbs = n / (a.elapsed_time(b) / 1e3) / 1e9
-    clk = roof["sm_count"] * roof["sm_max_mhz"] * 1e6
+    clk = n_sm * mhz * 1e6
     return {"gbs": gbs, "bytes_per_clk_per_sm": gbs * 1e9 / clk if clk else None,
-            "k1_frac_of_probe": roof["achieved"] / gbs,
-            "method": "tt_ctx_probe_l1: 8 blocks x 256 threads per SM, 32 coalesced 4-byte "
-                      "ld.global.nc per thread per iteration from a 16 KiB window, 5 x 4000 "
-                      "iterations, CUDA events; bytes per clock at the maximum SM clock"}
+            "method": "tt_ctx_probe_l1: one wave of resident 256-thread blocks, 32 coalesced 4-byte "
+                      "ld.global.nc per thread per iteration from a 24 KiB window (other lines "
+                      "every iteration), 5 x 4000 iterations, CUDA events; bytes per clock at "
+                      "the maximum SM clock"}
 
 
 def main():
@@ -814,11 +821,10 @@ def main():
     # roofline of the dominant kernel (semblance), from its live launch times
     roof = None
     if stats["timed_launches"] > 0 and stats["semblance_ms"] > 0:
-        roof = roofline(tt, ctx, prob, stats, args, clk)
+        roof = roofline(tt, ctx, prob, stats, args, clk, stream)
         roof["semblance_share_of_step"] = stats["semblance_ms"] / ms
         if rank == 0:
             roof["l2_probe"] = l2_probe(dev, stream)
-            roof["l1_probe"] = l1_probe(tt, ctx, stream, roof)
     # the same search in other forms on the same GPU (rank 0, line workload)
     comparison = None
     if rank == 0 and world == 1 and args.workload == "line" and not args.no_compare:

@@ -300,10 +300,11 @@ tt_status tt_ctx_stats(tt_ctx* ctx, tt_stats* out, int32_t reset);
 
 /* L1 load-bandwidth probe (no passage in the paper: a measurement aid for
  * the semblance kernel's roofline). Enqueues on `stream` one kernel in which
- * 8 blocks of 256 threads per SM each stream `iters` x 32 coalesced 4-byte
+ * one wave of resident 256-thread blocks (at most 8 per SM) each stream
+ * `iters` x 32 coalesced 4-byte
  * loads per thread (32 consecutive floats per warp request, the load K1
- * gathers its windows with) from a 16 KiB window of the context's scratch
- * that stays in L1 (32 warps resident per SM, as the semblance kernel);
+ * gathers its windows with) from a 24 KiB window of the context's scratch
+ * that stays in L1, each iteration at other lines of the window;
  * *bytes (host) receives the bytes it loads. Time it with events on
  * `stream`. It reads the scratch's contents, whatever they are, and may
  * write one float of it (the scratch holds nothing between launches).

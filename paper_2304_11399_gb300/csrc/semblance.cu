@@ -113,22 +113,21 @@ cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s) { return la
 
 // L1 load-bandwidth probe: every warp streams 4-byte loads (the instruction
 // K1 gathers its windows with), 32 consecutive floats per warp request, from
-// a 16 KiB window that stays in L1; the loads are volatile so that none is
-// hoisted out of the loop, and their sum is written so that none is dropped.
-// At most 64 registers, as K1: 32 warps resident per SM.
+// a 24 KiB window that stays in L1. Each iteration starts at another line of
+// the window (a multiple of 37 lines, modulo 64), so no load repeats an
+// earlier iteration's address and none can be moved out of the loop; their
+// sum is written so that none is dropped. The grid is one wave of resident
+// blocks (at most 8 of 256 threads per SM).
 constexpr int kProbeThreads = 256, kProbeBlocksPerSm = 8, kProbeLoads = 32;
 __global__ void __launch_bounds__(kProbeThreads, 4) k_l1_probe(const float* buf, int iters,
                                                                float* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float* base = buf + ((warp & 3) * 1024 + lane);
+  const float* base = buf + ((warp & 1) * 3072 + lane);
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int it = 0; it < iters; ++it) {
+    const float* p = base + ((it * 37) & 63) * 32;
 #pragma unroll
-    for (int u = 0; u < kProbeLoads; ++u) {
-      float v;
-      asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(base + u * 32));
-      acc[u & 7] += v;
-    }
+    for (int u = 0; u < kProbeLoads; ++u) acc[u & 7] += __ldg(p + u * 32);
   }
   float t = 0.f;
 #pragma unroll
@@ -138,7 +137,14 @@ __global__ void __launch_bounds__(kProbeThreads, 4) k_l1_probe(const float* buf,
 
 cudaError_t launch_l1_probe(const float* buf, float* out, int n_sm, int iters, double* bytes,
                             cudaStream_t s) {
-  const long long blocks = (long long)n_sm * kProbeBlocksPerSm;
+  // one wave: as many blocks as stay resident on every SM at once
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_l1_probe,
+                                                                kProbeThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > kProbeBlocksPerSm) per_sm = kProbeBlocksPerSm;
+  const long long blocks = (long long)n_sm * per_sm;
   *bytes = double(blocks) * kProbeThreads * double(iters) * kProbeLoads * sizeof(float);
   k_l1_probe<<<unsigned(blocks), kProbeThreads, 0, s>>>(buf, iters, out);
   return cudaGetLastError();
@@ -181,7 +187,7 @@ extern "C" tt_status tt_ctx_probe_l1(tt_ctx* ctx, int32_t iters, double* bytes, 
   if (iters < 1 || !bytes) return tt_fail(ctx, TT_ERR_INVALID_ARG, "iters < 1 or bytes is NULL");
   // the window and the sink live in the context's split scratch (no allocation)
   return tt_cuda_check(ctx,
-                       ctx->counted(tt::launch_l1_probe(ctx->split_part, ctx->split_part + 4096,
+                       ctx->counted(tt::launch_l1_probe(ctx->split_part, ctx->split_part + 8192,
                                                         ctx->n_sm, iters, bytes,
                                                         static_cast<cudaStream_t>(stream))),
                        "L1 probe launch");
