@@ -675,7 +675,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
-                    help="skip the plain-FP32 and BF16-stored comparison searches")
+                    help="skip every comparison entry (other forms, workloads and the ENS sweep)")
     ap.add_argument("--paper-compare", action="store_true",
                     help="also re-run the paper's ENS-vs-JADE experiment on the line (context, "
                          "off by default)")
