@@ -65,10 +65,16 @@ __device__ __forceinline__ bool unset(const float* th) { return isnan(th[0]); }
 // One thread per (local domain r, population slot i): the i-th present seed
 // in the order (t-1, t+1, previous trace, own best) -- only the previous
 // trace in the exploration stage -- or a random member drawn from Philox.
+// In the backward and forward stages the own best, the last seed, is not
+// evaluated again: its semblance at this sample is the stored best_S, written
+// to fit here, and skip[r] names its slot for the evaluation that follows
+// (every sample has a best once the exploration has passed, so the own best
+// is always there; were it not, the last slot would be passed over with a
+// NaN fitness, which ranks lowest).
 __global__ void k_ens_init(StepGeo g, int bf, int NP, int D, int* map, const float* best_th,
-                           float* pop, uint32_t key0, uint32_t key1, uint32_t gen,
-                           const float* lo, const float* hi, float* jade_mu, int* jade_na,
-                           float F0, float CR0) {
+                           const float* best_S, float* pop, float* fit, int* skip,
+                           uint32_t key0, uint32_t key1, uint32_t gen, const float* lo,
+                           const float* hi, float* jade_mu, int* jade_na, float F0, float CR0) {
   const long long n = (long long)g.n_buckets * g.n_est * NP;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
@@ -94,6 +100,11 @@ __global__ void k_ens_init(StepGeo g, int bf, int NP, int D, int* map, const flo
       seed[ns++] = best_th + (size_t)(d + 1) * D;
     if (has_prev && !unset(best_th + (size_t)dprev * D)) seed[ns++] = best_th + (size_t)dprev * D;
     if (!unset(best_th + (size_t)d * D)) seed[ns++] = best_th + (size_t)d * D;
+  }
+  if (bf && i == 0) {
+    const bool own = !unset(best_th + (size_t)d * D);
+    skip[r] = own ? ns - 1 : NP - 1;
+    fit[(size_t)r * NP + skip[r]] = own ? best_S[d] : __int_as_float(0x7fc00000);
   }
   float* out = pop + ((size_t)r * NP + i) * D;
   if (i < ns) {
@@ -205,6 +216,7 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
   cudaEvent_t* join_ev = c->side_ev + 2;  // [parity]: side work of that parity done
   bool side_busy[2] = {false, false};
   int* map_est = c->best_idx;
+  int* skip_est = c->slots + 2 * size_t(c->n_dom);  // [n_est] the own best's slot
   int* map_skp2[2] = {c->slots, c->slots + c->n_dom};
   float* th_skp2[2] = {c->imports, c->imports + size_t(c->n_dom) * D};
   float* S_skp2[2] = {c->pol_S, c->pol_bS};
@@ -241,12 +253,17 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
       if (g.n_est > 0) {
         const uint32_t gen0 = uint32_t(si + 1) * 65536u;
         k_ens_init<<<blocks((long long)n_est_loc * NP), 256, 0, s>>>(
-            g, sg.bf ? 1 : 0, NP, D, map_est, bth, c->pop, key0, key1, gen0, c->bounds,
-            c->bounds + D, c->cfg.adapt ? c->jade_mu : nullptr, c->jade_na, c->cfg.F, c->cfg.CR);
+            g, sg.bf ? 1 : 0, NP, D, map_est, bth, bS, c->pop, c->fit, skip_est, key0, key1,
+            gen0, c->bounds, c->bounds + D, c->cfg.adapt ? c->jade_mu : nullptr, c->jade_na,
+            c->cfg.F, c->cfg.CR);
         STEP(c->counted(cudaGetLastError()), "ens init");
         tt::EvalArgs ea = c->eval_args(c->pop, NP, c->fit);
         ea.n_dom = n_est_loc;
         ea.dom_map = map_est;
+        if (sg.bf) {  // the own best's semblance is known: NP - 1 pairs per sample
+          ea.P = NP - 1;
+          ea.skip_slot = skip_est;
+        }
         STEP(c->semblance(ea, s, false), "ens evaluate");
         calls += (unsigned long long)active * g.n_est * (sg.bf ? NP - 1 : NP);
         int cur = 0;
