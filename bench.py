@@ -389,8 +389,7 @@ def large_slab_compare(tt, dev, stream, n_slab=100, sample_frac=0.01):
 def batched_compare(tt, dev, stream):
     """The batched workload (4096 uneven CRS problems, 16-240 traces and
     750-3000 samples at 2 or 4 ms each, every sample a domain, DE 64 x 80):
-    one timed search with the autotuned kernel (the persistent work queue
-    for these uneven apertures) against the plain form (scalar kernel, one
+    one timed search with the autotuned kernel against the plain form (scalar kernel, one
     pair per thread, grid-mapped), on the same context and inputs; the two
     give identical results, so they are at the same accuracy."""
     from synth import configs

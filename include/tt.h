@@ -365,8 +365,12 @@ tt_status tt_ctx_get_option(const tt_ctx* ctx, int32_t option, int64_t* value);
  * scalar/128 -- on one evaluation of theta [n_dom][P][D] (S [n_dom][P]
  * receives it), keeps the fastest as the context's TT_OPT_KERNEL and
  * TT_OPT_BLOCK, and writes the mean time of each candidate in ms to
- * times_ms (host, TT_N_TUNE_CANDIDATES entries, may be NULL). Synchronises
- * `stream`. */
+ * times_ms (host, TT_N_TUNE_CANDIDATES entries, may be NULL). A persistent
+ * candidate is kept only if it is more than 3% faster than the fastest
+ * packed or scalar one; otherwise that one is kept (the persistent form's
+ * work queue gives up the L1 sharing between adjacent domains that a
+ * converged population has and a first-generation trial does not show).
+ * Synchronises `stream`. */
 tt_status tt_ctx_autotune(tt_ctx* ctx, const float* theta, int32_t P, float* S,
                           float* times_ms, void* stream);
 

@@ -122,6 +122,8 @@ extern "C" tt_status tt_ctx_get_option(const tt_ctx* c, int32_t option, int64_t*
   return tt_fail(nullptr, TT_ERR_INVALID_ARG, "unknown option %d", option);
 }
 
+constexpr float kPersistentMargin = 0.03f;
+
 extern "C" tt_status tt_ctx_autotune(tt_ctx* c, const float* theta, int32_t P, float* S,
                                      float* times_ms, void* stream) {
   if (!c) return tt_fail(nullptr, TT_ERR_INVALID_ARG, "ctx is NULL");
@@ -135,8 +137,7 @@ extern "C" tt_status tt_ctx_autotune(tt_ctx* c, const float* theta, int32_t P, f
   cudaError_t r = cudaEventCreate(&e0);
   if (r == cudaSuccess) r = cudaEventCreate(&e1);
   if (r != cudaSuccess) return tt_cuda_check(c, r, "event create");
-  int best = 0;
-  float best_ms = 0.f;
+  float t[TT_N_TUNE_CANDIDATES] = {};
   tt_status st = TT_OK;
   for (int i = 0; i < TT_N_TUNE_CANDIDATES && st == TT_OK; ++i) {
     tt::EvalArgs a = c->eval_args(theta, P, S);
@@ -153,16 +154,27 @@ extern "C" tt_status tt_ctx_autotune(tt_ctx* c, const float* theta, int32_t P, f
       st = tt_cuda_check(c, r, "autotune");
       break;
     }
-    ms /= 3.f;
-    if (times_ms) times_ms[i] = ms;
-    if (i == 0 || ms < best_ms) {
-      best = i;
-      best_ms = ms;
-    }
+    t[i] = ms / 3.f;
+    if (times_ms) times_ms[i] = t[i];
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != TT_OK) return st;
+  int best = 0;
+  for (int i = 1; i < TT_N_TUNE_CANDIDATES; ++i)
+    if (t[i] < t[best]) best = i;
+  // The trial population is usually a first generation, whose windows are
+  // scattered. Once a search's populations converge, the warps of a
+  // grid-mapped block (adjacent domains) read the same trace lines at the
+  // same time and share them in L1, which the work queue's scattered unit
+  // order loses; so the persistent form is kept only when it wins the trial
+  // by more than kPersistentMargin.
+  if (cand[best][0] == TT_KERNEL_PERSISTENT) {
+    int alt = -1;
+    for (int i = 0; i < TT_N_TUNE_CANDIDATES; ++i)
+      if (cand[i][0] != TT_KERNEL_PERSISTENT && (alt < 0 || t[i] < t[alt])) alt = i;
+    if (alt >= 0 && t[alt] <= t[best] * (1.f + kPersistentMargin)) best = alt;
+  }
   c->kernel = cand[best][0];
   c->block = cand[best][1];
   tt_ctx_drop_graph(c);

@@ -351,8 +351,9 @@ def tt_ctx_get_option(ctx: Context, option: str):
 
 
 def tt_ctx_autotune(ctx: Context, theta: torch.Tensor, stream=None):
-    """Time every kernel variant on theta [n_dom, P, D]; keep the fastest.
-    Returns {(variant, block): ms}."""
+    """Time every kernel variant on theta [n_dom, P, D] and keep the fastest,
+    except that a persistent variant is kept only when it is more than 3%
+    faster than the fastest packed or scalar one. Returns {(variant, block): ms}."""
     P = int(theta.shape[1])
     tp = _ptr(theta, "theta", shape=(ctx.n_dom, P, ctx.D))
     S = torch.empty((ctx.n_dom, P), dtype=torch.float32, device=theta.device)

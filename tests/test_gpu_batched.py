@@ -92,6 +92,10 @@ def test_batched_uneven_parity_all_variants(batch):
     times = tt.tt_ctx_autotune(ctx, to_dev(theta))
     assert set(times) == set(VARIANTS) and all(t > 0 for t in times.values())
     best = min(times, key=times.get)
+    if best[0] == "persistent":  # kept only when more than 3% ahead of the rest
+        alt = min((k for k in times if k[0] != "persistent"), key=times.get)
+        if times[alt] <= times[best] * (1 + np.float32(0.03)):
+            best = alt
     assert (tt.tt_ctx_get_option(ctx, "kernel"), tt.tt_ctx_get_option(ctx, "block")) == best
     S = tt.tt_semblance_eval(ctx, to_dev(theta)).cpu().numpy()
     assert np.array_equal(S, res["split"])  # a small launch: split by default
