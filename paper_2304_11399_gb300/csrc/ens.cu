@@ -67,12 +67,14 @@ __device__ __forceinline__ bool unset(const float* th) { return isnan(th[0]); }
 // trace in the exploration stage -- or a random member drawn from Philox.
 // In the backward and forward stages the own best, the last seed, is not
 // evaluated again: its semblance at this sample is the stored best_S, written
-// to fit here, and skip[r] names its slot for the evaluation that follows
-// (every sample has a best once the exploration has passed, so the own best
-// is always there; were it not, the last slot would be passed over with a
-// NaN fitness, which ranks lowest).
+// to fit here (every sample has a best once the exploration has passed, so the
+// own best is always there; were it not, the last slot would be passed over
+// with a NaN fitness, which ranks lowest). The other NP - 1 members are also
+// copied to the rows of cth [r][NP - 1][D], with cslot [r][NP - 1] naming each
+// one's slot in pop, so that the evaluation reads them contiguously and
+// scatters their semblance into fit.
 __global__ void k_ens_init(StepGeo g, int bf, int NP, int D, int* map, const float* best_th,
-                           const float* best_S, float* pop, float* fit, int* skip,
+                           const float* best_S, float* pop, float* fit, float* cth, int* cslot,
                            uint32_t key0, uint32_t key1, uint32_t gen, const float* lo,
                            const float* hi, float* jade_mu, int* jade_na, float F0, float CR0) {
   const long long n = (long long)g.n_buckets * g.n_est * NP;
@@ -101,19 +103,31 @@ __global__ void k_ens_init(StepGeo g, int bf, int NP, int D, int* map, const flo
     if (has_prev && !unset(best_th + (size_t)dprev * D)) seed[ns++] = best_th + (size_t)dprev * D;
     if (!unset(best_th + (size_t)d * D)) seed[ns++] = best_th + (size_t)d * D;
   }
-  if (bf && i == 0) {
-    const bool own = !unset(best_th + (size_t)d * D);
-    skip[r] = own ? ns - 1 : NP - 1;
-    fit[(size_t)r * NP + skip[r]] = own ? best_S[d] : __int_as_float(0x7fc00000);
-  }
   float* out = pop + ((size_t)r * NP + i) * D;
+  float* cout = nullptr;  // the member's compact row (none for the own best)
+  if (bf) {
+    const bool own = !unset(best_th + (size_t)d * D);
+    const int sk = own ? ns - 1 : NP - 1;
+    if (i == sk) {
+      fit[(size_t)r * NP + sk] = own ? best_S[d] : __int_as_float(0x7fc00000);
+    } else {
+      const size_t c = (size_t)r * (NP - 1) + (i > sk ? i - 1 : i);
+      cslot[c] = i;
+      cout = cth + c * D;
+    }
+  }
   if (i < ns) {
     for (int k = 0; k < D; ++k) out[k] = seed[i][k];
+    if (cout)
+      for (int k = 0; k < D; ++k) cout[k] = seed[i][k];
     return;
   }
   tt::Words w(key0, key1, uint32_t(d), gen, uint32_t(i), D);
-  for (int k = 0; k < D; ++k)
-    out[k] = __fadd_rn(lo[k], __fmul_rn(tt::unit_float(w.w[k]), __fsub_rn(hi[k], lo[k])));
+  for (int k = 0; k < D; ++k) {
+    const float v = __fadd_rn(lo[k], __fmul_rn(tt::unit_float(w.w[k]), __fsub_rn(hi[k], lo[k])));
+    out[k] = v;
+    if (cout) cout[k] = v;
+  }
 }
 
 // One warp per local domain: the population's best becomes the sample's best.
@@ -216,7 +230,10 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
   cudaEvent_t* join_ev = c->side_ev + 2;  // [parity]: side work of that parity done
   bool side_busy[2] = {false, false};
   int* map_est = c->best_idx;
-  int* skip_est = c->slots + 2 * size_t(c->n_dom);  // [n_est] the own best's slot
+  // compact rows and slot map of the evaluation that passes over the own best:
+  // the second trial buffers, which no step uses before its second generation
+  float* cth = c->trial[1];
+  int* cslot = reinterpret_cast<int*>(c->tfit[1]);
   int* map_skp2[2] = {c->slots, c->slots + c->n_dom};
   float* th_skp2[2] = {c->imports, c->imports + size_t(c->n_dom) * D};
   float* S_skp2[2] = {c->pol_S, c->pol_bS};
@@ -253,7 +270,7 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
       if (g.n_est > 0) {
         const uint32_t gen0 = uint32_t(si + 1) * 65536u;
         k_ens_init<<<blocks((long long)n_est_loc * NP), 256, 0, s>>>(
-            g, sg.bf ? 1 : 0, NP, D, map_est, bth, bS, c->pop, c->fit, skip_est, key0, key1,
+            g, sg.bf ? 1 : 0, NP, D, map_est, bth, bS, c->pop, c->fit, cth, cslot, key0, key1,
             gen0, c->bounds, c->bounds + D, c->cfg.adapt ? c->jade_mu : nullptr, c->jade_na,
             c->cfg.F, c->cfg.CR);
         STEP(c->counted(cudaGetLastError()), "ens init");
@@ -261,8 +278,10 @@ tt_status ens_body(tt_ctx* c, const tt_ens_cfg& e, float* bth, float* bS, cudaSt
         ea.n_dom = n_est_loc;
         ea.dom_map = map_est;
         if (sg.bf) {  // the own best's semblance is known: NP - 1 pairs per sample
+          ea.theta = cth;
           ea.P = NP - 1;
-          ea.skip_slot = skip_est;
+          ea.slots = cslot;
+          ea.np_out = NP;
         }
         STEP(c->semblance(ea, s, false), "ens evaluate");
         calls += (unsigned long long)active * g.n_est * (sg.bf ? NP - 1 : NP);

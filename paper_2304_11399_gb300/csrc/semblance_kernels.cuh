@@ -77,15 +77,6 @@ struct Lane {
   float umax;          // direct: u is clamped to ns + w
 };
 
-// Index of pair q's parameter vector and result in theta / S: q itself, or,
-// with a skipped member per domain, the domain's row of P + 1 members with
-// that member passed over.
-__device__ __forceinline__ long long pair_slot(const EvalArgs& a, long long q, int d) {
-  if (!a.skip_slot) return q;
-  const int i = int(q - (long long)d * a.P);
-  return (long long)d * (a.P + 1) + i + (i >= a.skip_slot[d] ? 1 : 0);
-}
-
 // L.d is the local domain (indexing theta and S); its geometry comes from the
 // global domain dom_map[L.d] when a map is given (a subset evaluation).
 template <int OP>
@@ -100,7 +91,7 @@ __device__ __forceinline__ bool lane_setup(const EvalArgs& a, long long q, Lane&
   L.e1 = a.ap_ptr[g + 1];
   L.p0i = a.dom_it0[gd];
   L.p0 = float(L.p0i);
-  const float* th = a.theta + pair_slot(a, q, L.d) * op_dim(OP);
+  const float* th = a.theta + q * op_dim(OP);
   const float i2 = L.inv_dt * L.inv_dt;
   L.cah = 0.f;
   L.cbh = 0.f;
@@ -219,7 +210,7 @@ __device__ __forceinline__ void store_S(const EvalArgs& a, long long q, int d, f
     const int slot = a.slots[q];
     if (slot >= 0) a.S[(size_t)d * a.np_out + slot] = S;
   } else {
-    a.S[pair_slot(a, q, d)] = S;
+    a.S[q] = S;
   }
 }
 

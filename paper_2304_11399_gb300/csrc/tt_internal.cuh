@@ -65,9 +65,6 @@ struct EvalArgs {
   const int* slots;         // scatter mode: result (d, p) -> S[d*np_out + slots[d*P+p]]
   int np_out;
   const int* dom_map;       // optional: local domain r -> global domain (-1: skip r)
-  const int* skip_slot;     // optional: per local domain, a member not evaluated; the P
-                            // pairs of domain d are then members 0..P of theta / S rows
-                            // of P + 1 (the skipped slot passed over)
   int kernel;               // TT_KERNEL_PACKED / _PERSISTENT / _SCALAR (forward launches)
   int block;                // threads per block: 128 or 256
   int split;                // 1: small forward launches split the aperture over warps
