@@ -729,7 +729,8 @@ def main():
         import synth
         from paper_2304_11399_gb300.slab import halo_exchange
         wl = configs.crs_line(0)
-        c0, c1 = synth.slab_bounds(wl.problem.n_m0, world, rank)
+        c0, c1 = synth.slab_bounds(wl.problem.n_m0, world, rank,
+                                   weights=np.diff(wl.problem.ap_ptr))  # equal work
         wl.traces, wl.mid, wl.off, wl.problem, base, hp, hn = synth.slab_problem(
             wl.line, c0, c1, half_window=5, ap_half=10)
         slab = (base, hp, hn, halo_exchange(rank, world))

@@ -196,13 +196,28 @@ def line_problem(line: Line, *, half_window: int, ap_half: int, cmps=None,
                    n_m0=G, n_t0=int(t0s.size))
 
 
-def slab_bounds(n_m0: int, world: int, rank: int):
+def slab_bounds(n_m0: int, world: int, rank: int, weights=None):
     """CMPs [c0, c1) of slab ``rank`` when n_m0 CMPs are cut into ``world``
-    contiguous slabs whose sizes differ by at most one (the first
-    n_m0 % world slabs take the extra CMP)."""
-    base, extra = divmod(n_m0, world)
-    c0 = rank * base + min(rank, extra)
-    return c0, c0 + base + (1 if rank < extra else 0)
+    contiguous slabs. Without ``weights`` the slabs' sizes differ by at most
+    one (the first n_m0 % world slabs take the extra CMP). With ``weights``
+    (the work of each CMP, e.g. its aperture's trace count: CMPs near the
+    line ends have clipped apertures) the r-th cut falls where the running
+    work is nearest to r / world of the total, every slab keeping at least
+    one CMP, so that the slabs carry about equal work."""
+    if weights is None:
+        base, extra = divmod(n_m0, world)
+        c0 = rank * base + min(rank, extra)
+        return c0, c0 + base + (1 if rank < extra else 0)
+    w = np.asarray(weights, dtype=np.float64)
+    if w.shape != (n_m0,) or world > n_m0 or np.any(w < 0):
+        raise ValueError("weights must give one non-negative value per CMP, world <= n_m0")
+    cum = np.concatenate([[0.0], np.cumsum(w)])
+    cuts = [0]
+    for r in range(1, world):
+        k = int(np.argmin(np.abs(cum - r * cum[-1] / world)))
+        cuts.append(min(max(k, cuts[-1] + 1), n_m0 - (world - r)))
+    cuts.append(n_m0)
+    return cuts[rank], cuts[rank + 1]
 
 
 def slab_problem(line: Line, c0: int, c1: int, *, half_window: int, ap_half: int):

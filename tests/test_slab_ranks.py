@@ -38,7 +38,13 @@ def _line(adapt):
     return wl
 
 
-def _worker(rank, world, port, adapt, out):
+def _weights(line):
+    """Work per CMP: the trace count of its aperture (clipped at the line ends)."""
+    import synth
+    return np.diff(synth.line_problem(line, half_window=5, ap_half=2).ap_ptr)
+
+
+def _worker(rank, world, port, adapt, weighted, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
     import torch
@@ -48,7 +54,8 @@ def _worker(rank, world, port, adapt, out):
     from paper_2304_11399_gb300.slab import halo_exchange
     dist.init_process_group("gloo", rank=rank, world_size=world)
     wl = _line(adapt)
-    c0, c1 = synth.slab_bounds(wl.line.n_cmp, world, rank)
+    c0, c1 = synth.slab_bounds(wl.line.n_cmp, world, rank,
+                               weights=_weights(wl.line) if weighted else None)
     tr, mid, off, prob, base, has_prev, has_next = synth.slab_problem(
         wl.line, c0, c1, half_window=5, ap_half=2)
     assert (has_prev, has_next) == (rank > 0, rank < world - 1)
@@ -67,15 +74,15 @@ def _worker(rank, world, port, adapt, out):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,adapt", [(2, 0), (3, 0), (2, 1)])
-def test_slabs_reproduce_the_whole_line_search(world, adapt):
+@pytest.mark.parametrize("world,adapt,weighted", [(2, 0, 0), (3, 0, 0), (2, 1, 0), (3, 0, 1)])
+def test_slabs_reproduce_the_whole_line_search(world, adapt, weighted):
     sys.path.insert(0, ROOT)
     import oracle
     wl = _line(adapt)
     th_ref, S_ref, n_ref = oracle.search.search(wl.traces, wl.mid, wl.off, wl.problem, wl.de)
     port = _free_port()
     out = mp.Manager().dict()
-    mp.spawn(_worker, args=(world, port, adapt, out), nprocs=world, join=True)
+    mp.spawn(_worker, args=(world, port, adapt, weighted, out), nprocs=world, join=True)
     parts = [out[r] for r in range(world)]
     assert [p[3] for p in parts] == sorted(p[3] for p in parts)
     th = np.concatenate([p[0] for p in parts])
@@ -111,6 +118,45 @@ def test_slab_inputs():
                 assert np.array_equal(tr[loc], line.traces[glob])
             seen += prob.n_dom
         assert seen == line.n_cmp * line.ns
+
+
+def test_work_weighted_slab_cuts():
+    """With per-CMP work weights the slabs are contiguous, non-empty, cover
+    the line, and each cut lies where the running work is nearest to its
+    share of the total (within half a CMP's weight of it unless a slab would
+    be empty); equal weights give the equal-size cut; on the line the edge
+    slabs, whose apertures are clipped, take more CMPs than the inner ones
+    and the largest slab's work does not exceed that of the equal-size cut."""
+    sys.path.insert(0, ROOT)
+    import synth
+    rng = np.random.default_rng(3)
+    for n, world in [(7, 3), (20, 4), (200, 8), (5, 5), (9, 1)]:
+        for w in (np.ones(n), rng.uniform(0.5, 2.0, n), np.r_[np.zeros(n - 1), 1.0]):
+            cuts = [synth.slab_bounds(n, world, r, weights=w) for r in range(world)]
+            assert cuts[0][0] == 0 and cuts[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(cuts, cuts[1:]))
+            assert all(c1 > c0 for c0, c1 in cuts)
+            cum = np.concatenate([[0.0], np.cumsum(w)])
+            for r in range(1, world):
+                k, target = cuts[r][0], r * cum[-1] / world
+                clamped = k == cuts[r - 1][0] + 1 or k == n - (world - r)
+                assert clamped or abs(cum[k] - target) <= w.max() / 2 + 1e-9
+            if np.all(w == 1) and n % world == 0:
+                assert cuts == [synth.slab_bounds(n, world, r) for r in range(world)]
+    from synth import configs
+    big = configs.crs_line(4, n_cmp=200, ns=60, n_events=2, ap_half=10, np_=8, ng=6,
+                           exch_every=2, polish_steps=1, tau_max=0.22)
+    w = np.diff(big.problem.ap_ptr)
+    sizes = [c1 - c0 for c0, c1 in (synth.slab_bounds(200, 8, r, weights=w) for r in range(8))]
+    assert sizes[0] > 25 and sizes[-1] > 25 and max(sizes[1:-1]) <= 25
+    for world in (4, 8):  # the largest slab's work never grows; at 4 slabs it shrinks
+        work = [w[c0:c1].sum() for c0, c1 in (synth.slab_bounds(200, world, r, weights=w)
+                                              for r in range(world))]
+        eq = [w[c0:c1].sum() for c0, c1 in (synth.slab_bounds(200, world, r)
+                                            for r in range(world))]
+        assert max(work) < max(eq) if world == 4 else max(work) <= max(eq)
+    with pytest.raises(ValueError):
+        synth.slab_bounds(3, 4, 0, weights=np.ones(3))
 
 
 def test_the_halo_rows_matter():
