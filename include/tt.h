@@ -254,7 +254,10 @@ tt_status tt_polish(tt_ctx* ctx, float* theta, float* S, int32_t steps, float lr
  * cycles (NP_bf x NG_bf, seeded with the bests of samples t-1, t+1, of
  * sample t on the previous trace of the sweep, and the own best); each stage
  * estimates every (n_skip+1)-th sample and interpolates the others linearly
- * in t, keeping the higher semblance (Sec. 3.5). */
+ * in t, keeping the higher semblance (Sec. 3.5). In the backward-and-forward
+ * stages a sample's own best seed is not evaluated again: its stored
+ * semblance is its fitness (the call count of eq. ens_semblance leaves it
+ * out as well). */
 typedef struct tt_ens_cfg {
   int32_t np_f, ng_f;    /* forward exploration: population, generations      */
   int32_t np_bf, ng_bf;  /* backward-and-forward stages                       */
