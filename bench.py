@@ -517,6 +517,7 @@ def run_reference(args):
 # ends), no re-reads.
 K1_LINE_DRAM_BYTES = 297_862_059 + 61_190_827
 K1_LINE_DRAM_KERNEL = "packed/128"
+K1_LINE_DRAM_MEMBER_ORDER = False  # the capture's launch form (index order)
 
 
 def hbm_peak_gbs():
@@ -610,8 +611,10 @@ def roofline(tt, ctx, prob, stats, args, clk, stream):
     probe = l1_probe(tt, ctx, stream, n_sm, mhz)
     peak = probe["gbs"]
     kern = f"{tt.tt_ctx_get_option(ctx, 'kernel')}/{tt.tt_ctx_get_option(ctx, 'block')}"
+    same_form = (kern == K1_LINE_DRAM_KERNEL and
+                 tt.tt_ctx_get_option(ctx, "member_order") == K1_LINE_DRAM_MEMBER_ORDER)
     traffic = (K1_LINE_DRAM_BYTES if (args.workload == "line" and args.storage == "f32" and
-                                      not args.cmps and kern == K1_LINE_DRAM_KERNEL) else None)
+                                      not args.cmps and same_form) else None)
     fp32_peak = n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
     op = int(prob.op)
     roof = {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -341,10 +341,19 @@ tt_status tt_ctx_probe_l1(tt_ctx* ctx, int32_t iters, double* bytes, void* strea
  *                 still does not depend on TT_OPT_KERNEL / TT_OPT_BLOCK, but
  *                 its rounding differs from the unsplit kernels' (all stay
  *                 within 1e-5 of the exact semblance). The smallest launches
- *                 also spread a unit over up to 4 blocks that combine their
+ *                 also spread a unit over up to 9 blocks that combine their
  *                 sums through the context's scratch, so split evaluations on
  *                 one context must not overlap on the GPU (one stream, or
  *                 events between streams). 0: never split.
+ *  TT_OPT_MEMBER_ORDER  1 (default): before each generation's evaluation
+ *                 inside tt_search / tt_search_slab (NP <= 256), the members
+ *                 of every domain are put in the order of their window
+ *                 position on the domain's middle aperture entry, so that the
+ *                 lanes of a warp read windows that lie close together; the
+ *                 results go back to each member's own slot, and S, the
+ *                 search and its call count are bit-identical to 0 (the
+ *                 index order). The reordered copy uses the trial buffer that
+ *                 the generation's selection has just consumed.
  *  TT_OPT_SPLIT_MAX_PAIRS  (read only) the split threshold above, in pairs.
  *  TT_OPT_SM_COUNT  (read only) multiprocessors of the context's device,
  *                 queried at tt_ctx_create; the split thresholds and the
@@ -356,7 +365,8 @@ enum {
   TT_OPT_SEARCH_GRAPH = 3,
   TT_OPT_SPLIT = 4,
   TT_OPT_SPLIT_MAX_PAIRS = 5,
-  TT_OPT_SM_COUNT = 6
+  TT_OPT_SM_COUNT = 6,
+  TT_OPT_MEMBER_ORDER = 7
 };
 enum { TT_KERNEL_PACKED = 1, TT_KERNEL_PERSISTENT = 2, TT_KERNEL_SCALAR = 3 };
 #define TT_N_TUNE_CANDIDATES 6

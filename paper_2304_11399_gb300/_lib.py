@@ -11,7 +11,7 @@ TT_OK, TT_ERR_INVALID_ARG, TT_ERR_CUDA, TT_ERR_OUT_OF_MEMORY, TT_ERR_TIMEOUT, \
     TT_ERR_UNSUPPORTED = range(6)
 TT_OP_CMP, TT_OP_CRS, TT_OP_FOCRS = 0, 1, 2
 TT_OPT_KERNEL, TT_OPT_BLOCK, TT_OPT_SEARCH_GRAPH, TT_OPT_SPLIT = 1, 2, 3, 4
-TT_OPT_SPLIT_MAX_PAIRS, TT_OPT_SM_COUNT = 5, 6
+TT_OPT_SPLIT_MAX_PAIRS, TT_OPT_SM_COUNT, TT_OPT_MEMBER_ORDER = 5, 6, 7
 TT_KERNEL_PACKED, TT_KERNEL_PERSISTENT, TT_KERNEL_SCALAR = 1, 2, 3
 TT_N_TUNE_CANDIDATES = 6
 TUNE_CANDIDATES = [("packed", 256), ("packed", 128), ("persistent", 256), ("persistent", 128),

@@ -99,6 +99,9 @@ extern "C" tt_status tt_ctx_set_option(tt_ctx* c, int32_t option, int64_t value)
     case TT_OPT_SPLIT:
       c->split = value != 0;
       break;
+    case TT_OPT_MEMBER_ORDER:
+      c->member_order = value != 0;
+      break;
     case TT_OPT_SPLIT_MAX_PAIRS:
     case TT_OPT_SM_COUNT:
       return tt_fail(c, TT_ERR_INVALID_ARG, "option %d is read only", option);
@@ -116,6 +119,7 @@ extern "C" tt_status tt_ctx_get_option(const tt_ctx* c, int32_t option, int64_t*
     case TT_OPT_BLOCK: *value = c->block; return TT_OK;
     case TT_OPT_SEARCH_GRAPH: *value = c->use_graph ? 1 : 0; return TT_OK;
     case TT_OPT_SPLIT: *value = c->split ? 1 : 0; return TT_OK;
+    case TT_OPT_MEMBER_ORDER: *value = c->member_order ? 1 : 0; return TT_OK;
     case TT_OPT_SPLIT_MAX_PAIRS: *value = (int64_t)c->n_sm * tt::kSplitUnitsPerSm * 64; return TT_OK;
     case TT_OPT_SM_COUNT: *value = c->n_sm; return TT_OK;
   }

@@ -94,12 +94,31 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
     d.dom_base = base;
     return d;
   };
+  // Evaluate population th [n_dom][NP] into fit, in member order when the
+  // option is on: the order kernel writes the reordered copy and its slot map
+  // to the free trial buffers (tmp, tmp_fit), and the evaluation scatters
+  // each member's semblance back to its own slot.
+  const bool order = c->member_order && NP > 1 && NP <= tt::kOrderMaxP;
+  auto evaluate = [&](const float* th, float* fit, float* tmp, float* tmp_fit) -> tt_status {
+    if (!order) return tt_cuda_check(c, c->semblance(c->eval_args(th, NP, fit), s, false),
+                                     "evaluate");
+    int* map = reinterpret_cast<int*>(tmp_fit);
+    tt_status r = tt_cuda_check(
+        c, c->counted(tt::launch_member_order(c->eval_args(th, NP, nullptr), tmp, map, s)),
+        "member order");
+    if (r != TT_OK) return r;
+    tt::EvalArgs ea = c->eval_args(tmp, NP, fit);
+    ea.slots = map;
+    ea.np_out = NP;
+    return tt_cuda_check(c, c->semblance(ea, s, false), "evaluate");
+  };
   // generation 0: initialise and evaluate
   tt::DeArgs a = de_args(0);
   a.pop = c->pop;
   a.fit = c->fit;
   STEP(c->counted(tt::launch_de_step(a, s)), "init");
-  STEP(c->semblance(c->eval_args(c->pop, NP, c->fit), s, false), "evaluate init");
+  st = evaluate(c->pop, c->fit, c->trial[0], c->tfit[0]);
+  if (st != TT_OK) return st;
   evals += (unsigned long long)NP * c->n_dom;
   int cur = 0;            // trial buffer written by the next mutation
   bool pending = false;   // trial[cur ^ 1] awaits selection
@@ -111,7 +130,9 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
     a.tfit = pending ? c->tfit[cur ^ 1] : nullptr;
     a.next = c->trial[cur];
     STEP(c->counted(tt::launch_de_step(a, s)), "de step");
-    STEP(c->semblance(c->eval_args(c->trial[cur], NP, c->tfit[cur]), s, false), "evaluate");
+    // the selection above has consumed trial[cur ^ 1]: free for the reordered copy
+    st = evaluate(c->trial[cur], c->tfit[cur], c->trial[cur ^ 1], c->tfit[cur ^ 1]);
+    if (st != TT_OK) return st;
     evals += (unsigned long long)NP * c->n_dom;
     pending = true;
     cur ^= 1;

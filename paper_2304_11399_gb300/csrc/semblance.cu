@@ -11,6 +11,9 @@ extern template KFn pick_kernel<TT_OP_FOCRS>(int, int, int, bool);
 extern template SFn pick_stack<TT_OP_CMP>(int, bool);
 extern template SFn pick_stack<TT_OP_CRS>(int, bool);
 extern template SFn pick_stack<TT_OP_FOCRS>(int, bool);
+extern template OFn pick_order<TT_OP_CMP>(bool);
+extern template OFn pick_order<TT_OP_CRS>(bool);
+extern template OFn pick_order<TT_OP_FOCRS>(bool);
 }  // namespace sk
 
 namespace {
@@ -110,6 +113,24 @@ cudaError_t launch_stack(const EvalArgs& a, float* out, cudaStream_t s) {
 }
 
 cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s) { return launch(a, s, true); }
+
+cudaError_t launch_member_order(const EvalArgs& a, float* theta_out, int* slots,
+                                cudaStream_t s) {
+  if (a.n_dom == 0) return cudaSuccess;
+  if (a.P < 1 || a.P > kOrderMaxP || a.dom_map) return cudaErrorInvalidValue;
+  const bool mv = a.umax > float(kDirectMax);
+  sk::OFn fn = nullptr;
+  switch (a.op) {
+    case TT_OP_CMP: fn = sk::pick_order<TT_OP_CMP>(mv); break;
+    case TT_OP_CRS: fn = sk::pick_order<TT_OP_CRS>(mv); break;
+    case TT_OP_FOCRS: fn = sk::pick_order<TT_OP_FOCRS>(mv); break;
+  }
+  if (!fn) return cudaErrorInvalidValue;
+  const long long blocks = ((long long)a.n_dom + sk::kOrderWarps - 1) / sk::kOrderWarps;
+  if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+  fn<<<unsigned(blocks), 32 * sk::kOrderWarps, 0, s>>>(a, theta_out, slots);
+  return cudaGetLastError();
+}
 
 // L1 load-bandwidth probe: every warp streams 4-byte loads (the instruction
 // K1 gathers its windows with), 32 consecutive floats per warp request, from

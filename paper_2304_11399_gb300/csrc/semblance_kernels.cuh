@@ -697,6 +697,58 @@ __global__ void __launch_bounds__(256) k_stack(const EvalArgs a, float* __restri
   }
 }
 
+// Member order of one population for the evaluation that follows: one warp
+// per domain ranks the domain's P members (P <= kOrderMaxP) by the position
+// of their window on the domain's middle aperture entry (ties by index; an
+// empty aperture keeps the index order), then writes member i's parameters
+// to row rank(i) of theta_out and i to slots[d * P + rank(i)]. Evaluating
+// theta_out with those slots as the scatter map gives every member its own
+// semblance bit for bit (a pair's arithmetic does not depend on its lane),
+// while the 32 lanes of a warp read windows that lie close together.
+constexpr int kOrderWarps = 8;
+
+template <int OP, bool MV>
+__global__ void __launch_bounds__(32 * kOrderWarps) k_member_order(const EvalArgs a,
+                                                                   float* __restrict__ theta_out,
+                                                                   int* __restrict__ slots) {
+  __shared__ float key[kOrderWarps][kOrderMaxP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long d = (long long)blockIdx.x * kOrderWarps + w;
+  if (d >= a.n_dom) return;  // warp-uniform
+  const int P = a.P;
+  for (int i = lane; i < P; i += 32) {
+    Lane L;
+    float k = 0.f;
+    if (lane_setup<OP>(a, d * P + i, L) && L.e1 > L.e0) {
+      k = locate<OP, MV>(L, __ldg(a.ap_tab + ((L.e0 + L.e1) >> 1))).u;
+      if (!(k == k)) k = 3.0e38f;
+    }
+    key[w][i] = k;
+  }
+  __syncwarp();
+  constexpr int D = op_dim(OP);
+  for (int i = lane; i < P; i += 32) {
+    const float ki = key[w][i];
+    int rank = 0;
+    for (int j = 0; j < P; ++j) {
+      const float kj = key[w][j];
+      rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+    }
+    const float* src = a.theta + (d * P + i) * D;
+    float* dst = theta_out + (d * P + rank) * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) dst[k] = src[k];
+    slots[d * P + rank] = i;
+  }
+}
+
+using OFn = void (*)(const EvalArgs, float*, int*);
+
+template <int OP>
+OFn pick_order(bool mv) {
+  return mv ? k_member_order<OP, true> : k_member_order<OP, false>;
+}
+
 using SFn = void (*)(const EvalArgs, float*);
 enum KernelKind { kKindPacked = 0, kKindScalar = 1, kKindSplit = 2, kKindGrad = 3 };
 

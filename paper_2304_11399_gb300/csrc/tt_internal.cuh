@@ -46,6 +46,7 @@ constexpr int kSplitPartStride = 2 * 8 + 2;  // floats per pair: K + 1 for the w
 constexpr int kPadFront = 8;
 constexpr int kPadBack = 24;
 constexpr int kBlock = 256;
+constexpr int kOrderMaxP = 256;  // largest population the member order handles
 
 inline int padded_pitch(int ns) { return ((kPadFront + ns + kPadBack) + 15) / 16 * 16; }
 
@@ -78,6 +79,11 @@ struct EvalArgs {
 
 cudaError_t launch_semblance(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_semblance_grad(const EvalArgs& a, cudaStream_t s);
+// Members of each domain of theta (a.theta, a.P <= 256, no domain map) sorted
+// by window position: parameters to theta_out, original slots to slots
+// ([n_dom][P]); evaluate theta_out with slots as the scatter map.
+cudaError_t launch_member_order(const EvalArgs& a, float* theta_out, int* slots,
+                                cudaStream_t s);
 cudaError_t launch_stack(const EvalArgs& a, float* out, cudaStream_t s);
 cudaError_t launch_l1_probe(const float* buf, float* out, int n_sm, int iters, double* bytes,
                             cudaStream_t s);
@@ -230,6 +236,7 @@ struct tt_ctx {
   // launch configuration (tt_ctx_set_option / tt_ctx_autotune)
   int kernel = TT_KERNEL_PACKED, block = 256;
   bool split = true;  // TT_OPT_SPLIT
+  bool member_order = true;  // TT_OPT_MEMBER_ORDER
   bool use_graph = true;
   // CUDA graph of the whole search, captured on first use
   cudaStream_t cap_stream = nullptr;

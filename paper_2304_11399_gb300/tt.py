@@ -322,8 +322,10 @@ _KERNELS = {"packed": L.TT_KERNEL_PACKED, "persistent": L.TT_KERNEL_PERSISTENT,
 
 def tt_ctx_set_option(ctx: Context, option: str, value):
     """option: "kernel" ("packed" | "persistent" | "scalar"), "block" (128 | 256),
-    "search_graph" (bool) or "split" (bool: split the aperture over the warps
-    of a block for launches of fewer than the "split_max_pairs" threshold)."""
+    "search_graph" (bool), "split" (bool: split the aperture over the warps
+    of a block for launches of fewer than the "split_max_pairs" threshold) or
+    "member_order" (bool: the search evaluates each domain's members in the
+    order of their window position; same results)."""
     if option == "kernel":
         code, v = L.TT_OPT_KERNEL, _KERNELS[value]
     elif option == "block":
@@ -332,6 +334,8 @@ def tt_ctx_set_option(ctx: Context, option: str, value):
         code, v = L.TT_OPT_SEARCH_GRAPH, 1 if value else 0
     elif option == "split":
         code, v = L.TT_OPT_SPLIT, 1 if value else 0
+    elif option == "member_order":
+        code, v = L.TT_OPT_MEMBER_ORDER, 1 if value else 0
     else:
         raise ValueError(f"unknown option {option}")
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_set_option(ctx.handle, code, v))
@@ -342,12 +346,13 @@ def tt_ctx_get_option(ctx: Context, option: str):
     (split threshold in pairs) and "sm_count" (the device's multiprocessors)."""
     code = {"kernel": L.TT_OPT_KERNEL, "block": L.TT_OPT_BLOCK,
             "search_graph": L.TT_OPT_SEARCH_GRAPH, "split": L.TT_OPT_SPLIT,
+            "member_order": L.TT_OPT_MEMBER_ORDER,
             "split_max_pairs": L.TT_OPT_SPLIT_MAX_PAIRS, "sm_count": L.TT_OPT_SM_COUNT}[option]
     v = C.c_int64()
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_get_option(ctx.handle, code, C.byref(v)))
     if option == "kernel":
         return {b: a for a, b in _KERNELS.items()}[v.value]
-    return bool(v.value) if option in ("search_graph", "split") else int(v.value)
+    return bool(v.value) if option in ("search_graph", "split", "member_order") else int(v.value)
 
 
 def tt_ctx_autotune(ctx: Context, theta: torch.Tensor, stream=None):
