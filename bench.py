@@ -512,12 +512,23 @@ def run_reference(args):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 #       --clock-control none -k regex:k_semblance -s 40 -c 3
 #       python bench.py --steps 1 --warmup 0 --no-e2e --no-cpu-baseline --no-compare
-# 297.9 MB read + 61.2 MB written: the compulsory bytes (theta 230.4 MB and the
-# 57.6 MB line read, S 76.8 MB written, part of it still in L2 when the launch
-# ends), no re-reads.
-K1_LINE_DRAM_BYTES = 297_862_059 + 61_190_827
+# with the members in window order (mean of three generation launches):
+# 375.0 MB read + 63.5 MB written: the compulsory bytes (theta 230.4 MB, the
+# 57.6 MB line and the 76.8 MB slot map read, S 76.8 MB written, part of it
+# still in L2 when the launch ends), no re-reads.
+K1_LINE_DRAM_BYTES = 374_962_517 + 63_500_629
 K1_LINE_DRAM_KERNEL = "packed/128"
-K1_LINE_DRAM_MEMBER_ORDER = False  # the capture's launch form (index order)
+K1_LINE_DRAM_MEMBER_ORDER = True  # the capture's launch form: members in window order
+
+
+def member_order_on(tt, ctx, prob):
+    """Whether the search evaluates members in window order: the option, or
+    for "auto" the library's rule (mean aperture of at least 768 traces)."""
+    opt = tt.tt_ctx_get_option(ctx, "member_order")
+    if opt == "auto":
+        ap = np.diff(np.asarray(prob.ap_ptr))[np.asarray(prob.dom_group)]
+        return bool(ap.size) and float(ap.mean()) >= 768.0
+    return bool(opt)
 
 
 def hbm_peak_gbs():
@@ -612,7 +623,7 @@ def roofline(tt, ctx, prob, stats, args, clk, stream):
     peak = probe["gbs"]
     kern = f"{tt.tt_ctx_get_option(ctx, 'kernel')}/{tt.tt_ctx_get_option(ctx, 'block')}"
     same_form = (kern == K1_LINE_DRAM_KERNEL and
-                 tt.tt_ctx_get_option(ctx, "member_order") == K1_LINE_DRAM_MEMBER_ORDER)
+                 member_order_on(tt, ctx, prob) == K1_LINE_DRAM_MEMBER_ORDER)
     traffic = (K1_LINE_DRAM_BYTES if (args.workload == "line" and args.storage == "f32" and
                                       not args.cmps and same_form) else None)
     fp32_peak = n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
@@ -891,6 +902,7 @@ def main():
                 "config": workload_config(wl, world), "clocks": clk, "e2e": e2e,
                 "gpu_launches": int(stats["launches"]), "semblance_calls_per_step": n_evals,
                 "roofline": roof, "cpu_baseline": cpu, "comparison": comparison}
+        line["config"]["member_order"] = member_order_on(tt, ctx, prob)
         if tuned:
             line["config"]["autotune_ms"] = tuned
             line["config"]["kernel"] = (f"{tt.tt_ctx_get_option(ctx, 'kernel')}/"

@@ -345,15 +345,18 @@ tt_status tt_ctx_probe_l1(tt_ctx* ctx, int32_t iters, double* bytes, void* strea
  *                 sums through the context's scratch, so split evaluations on
  *                 one context must not overlap on the GPU (one stream, or
  *                 events between streams). 0: never split.
- *  TT_OPT_MEMBER_ORDER  1 (default): before each generation's evaluation
- *                 inside tt_search / tt_search_slab (NP <= 256), the members
- *                 of every domain are put in the order of their window
- *                 position on the domain's middle aperture entry, so that the
- *                 lanes of a warp read windows that lie close together; the
- *                 results go back to each member's own slot, and S, the
- *                 search and its call count are bit-identical to 0 (the
- *                 index order). The reordered copy uses the trial buffer that
- *                 the generation's selection has just consumed.
+ *  TT_OPT_MEMBER_ORDER  1: before each generation's evaluation inside
+ *                 tt_search / tt_search_slab (NP <= 256), the members of
+ *                 every domain are put in the order of their window position
+ *                 on the domain's middle aperture entry, so that the lanes of
+ *                 a warp read windows that lie close together; the results go
+ *                 back to each member's own slot, and S, the search and its
+ *                 call count are bit-identical to 0 (the index order). The
+ *                 reordered copy uses the trial buffer that the generation's
+ *                 selection has just consumed. 2 (default): 1 when the
+ *                 apertures hold at least 768 traces on average (long
+ *                 apertures scatter the members' windows most and carry the
+ *                 most work per member), else 0.
  *  TT_OPT_SPLIT_MAX_PAIRS  (read only) the split threshold above, in pairs.
  *  TT_OPT_SM_COUNT  (read only) multiprocessors of the context's device,
  *                 queried at tt_ctx_create; the split thresholds and the

@@ -100,7 +100,9 @@ extern "C" tt_status tt_ctx_set_option(tt_ctx* c, int32_t option, int64_t value)
       c->split = value != 0;
       break;
     case TT_OPT_MEMBER_ORDER:
-      c->member_order = value != 0;
+      if (value < 0 || value > 2)
+        return tt_fail(c, TT_ERR_INVALID_ARG, "member order must be 0, 1 or 2 (automatic)");
+      c->member_order = int(value);
       break;
     case TT_OPT_SPLIT_MAX_PAIRS:
     case TT_OPT_SM_COUNT:
@@ -119,7 +121,7 @@ extern "C" tt_status tt_ctx_get_option(const tt_ctx* c, int32_t option, int64_t*
     case TT_OPT_BLOCK: *value = c->block; return TT_OK;
     case TT_OPT_SEARCH_GRAPH: *value = c->use_graph ? 1 : 0; return TT_OK;
     case TT_OPT_SPLIT: *value = c->split ? 1 : 0; return TT_OK;
-    case TT_OPT_MEMBER_ORDER: *value = c->member_order ? 1 : 0; return TT_OK;
+    case TT_OPT_MEMBER_ORDER: *value = c->member_order; return TT_OK;
     case TT_OPT_SPLIT_MAX_PAIRS: *value = (int64_t)c->n_sm * tt::kSplitUnitsPerSm * 64; return TT_OK;
     case TT_OPT_SM_COUNT: *value = c->n_sm; return TT_OK;
   }

@@ -98,7 +98,9 @@ tt_status search_body(tt_ctx* c, float* best_theta, float* best_S, cudaStream_t 
   // option is on: the order kernel writes the reordered copy and its slot map
   // to the free trial buffers (tmp, tmp_fit), and the evaluation scatters
   // each member's semblance back to its own slot.
-  const bool order = c->member_order && NP > 1 && NP <= tt::kOrderMaxP;
+  const bool long_apertures = c->sum_N >= tt::kOrderMinMeanAperture * double(c->n_dom);
+  const bool order = (c->member_order == 1 || (c->member_order == 2 && long_apertures)) &&
+                     NP > 1 && NP <= tt::kOrderMaxP;
   auto evaluate = [&](const float* th, float* fit, float* tmp, float* tmp_fit) -> tt_status {
     if (!order) return tt_cuda_check(c, c->semblance(c->eval_args(th, NP, fit), s, false),
                                      "evaluate");

@@ -47,6 +47,8 @@ constexpr int kPadFront = 8;
 constexpr int kPadBack = 24;
 constexpr int kBlock = 256;
 constexpr int kOrderMaxP = 256;  // largest population the member order handles
+// automatic member order: on when the mean aperture holds at least this many traces
+constexpr double kOrderMinMeanAperture = 768.0;
 
 inline int padded_pitch(int ns) { return ((kPadFront + ns + kPadBack) + 15) / 16 * 16; }
 
@@ -236,7 +238,7 @@ struct tt_ctx {
   // launch configuration (tt_ctx_set_option / tt_ctx_autotune)
   int kernel = TT_KERNEL_PACKED, block = 256;
   bool split = true;  // TT_OPT_SPLIT
-  bool member_order = true;  // TT_OPT_MEMBER_ORDER
+  int member_order = 2;  // TT_OPT_MEMBER_ORDER: 0 index order, 1 member order, 2 automatic
   bool use_graph = true;
   // CUDA graph of the whole search, captured on first use
   cudaStream_t cap_stream = nullptr;

@@ -324,8 +324,10 @@ def tt_ctx_set_option(ctx: Context, option: str, value):
     """option: "kernel" ("packed" | "persistent" | "scalar"), "block" (128 | 256),
     "search_graph" (bool), "split" (bool: split the aperture over the warps
     of a block for launches of fewer than the "split_max_pairs" threshold) or
-    "member_order" (bool: the search evaluates each domain's members in the
-    order of their window position; same results)."""
+    "member_order" (True: the search evaluates each domain's members in the
+    order of their window position, same results; False: index order;
+    "auto", the default: True when the apertures hold at least 768 traces
+    on average)."""
     if option == "kernel":
         code, v = L.TT_OPT_KERNEL, _KERNELS[value]
     elif option == "block":
@@ -335,7 +337,7 @@ def tt_ctx_set_option(ctx: Context, option: str, value):
     elif option == "split":
         code, v = L.TT_OPT_SPLIT, 1 if value else 0
     elif option == "member_order":
-        code, v = L.TT_OPT_MEMBER_ORDER, 1 if value else 0
+        code, v = L.TT_OPT_MEMBER_ORDER, 2 if value == "auto" else (1 if value else 0)
     else:
         raise ValueError(f"unknown option {option}")
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_set_option(ctx.handle, code, v))
@@ -352,7 +354,9 @@ def tt_ctx_get_option(ctx: Context, option: str):
     _check(ctx.lib, ctx.handle, ctx.lib.tt_ctx_get_option(ctx.handle, code, C.byref(v)))
     if option == "kernel":
         return {b: a for a, b in _KERNELS.items()}[v.value]
-    return bool(v.value) if option in ("search_graph", "split", "member_order") else int(v.value)
+    if option == "member_order":
+        return "auto" if v.value == 2 else bool(v.value)
+    return bool(v.value) if option in ("search_graph", "split") else int(v.value)
 
 
 def tt_ctx_autotune(ctx: Context, theta: torch.Tensor, stream=None):

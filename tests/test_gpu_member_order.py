@@ -1,5 +1,6 @@
 """The search with members evaluated in the order of their window position
-(TT_OPT_MEMBER_ORDER, the default) against the index order: the order only
+(TT_OPT_MEMBER_ORDER = 1; the default orders them when apertures are long)
+against the index order: the order only
 changes which lane evaluates which member, so best parameters, semblance and
 call counts must be identical bit for bit -- on launches that fill the GPU
 (the packed kernel) and on small ones (the split kernel), for the CRS, CMP
@@ -49,10 +50,34 @@ def _line(seed, n_cmp, **kw):
     return configs.crs_line(seed, n_cmp=n_cmp, **kw)
 
 
-def test_default_is_on():
-    wl = _line(1, 3, ng=1)
+def _launches(wl, order):
     ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, wl.problem, wl.de, device=dev())
-    assert tt.tt_ctx_get_option(ctx, "member_order") is True
+    if order is not None:
+        tt.tt_ctx_set_option(ctx, "member_order", order)
+    assert tt.tt_ctx_get_option(ctx, "member_order") == ("auto" if order is None else order)
+    tt.tt_ctx_set_option(ctx, "search_graph", False)
+    tt.tt_ctx_stats(ctx, reset=True)
+    tt.tt_search(ctx)
+    n = tt.tt_ctx_stats(ctx)["launches"]
+    ctx.close()
+    return n
+
+
+def test_automatic_order_follows_the_mean_aperture():
+    """The default ("auto") orders the members, one extra launch per
+    evaluated population (NG + 1), only when the apertures hold at least 768
+    traces on average."""
+    for ap_half, n_cmp in ((3, 6), (10, 24)):
+        wl = _line(1, n_cmp, ap_half=ap_half, ng=3, exch_every=0, polish_steps=0)
+        mean_ap = float((wl.problem.ap_ptr[1:] - wl.problem.ap_ptr[:-1]).mean())
+        off, on, auto = (_launches(wl, o) for o in (False, True, None))
+        assert on == off + wl.de.ng + 1
+        assert auto == (on if mean_ap >= 768 else off)
+    assert mean_ap >= 768  # the second line exercises the ordered default
+    from paper_2304_11399_gb300 import _lib as L
+    ctx = tt.tt_ctx_create(wl.traces, wl.mid, wl.off, wl.problem, wl.de, device=dev())
+    assert ctx.lib.tt_ctx_set_option(ctx.handle, L.TT_OPT_MEMBER_ORDER, 3) == L.TT_ERR_INVALID_ARG
+    assert tt.tt_ctx_get_option(ctx, "member_order") == "auto"
     ctx.close()
 
 
