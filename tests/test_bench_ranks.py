@@ -93,3 +93,37 @@ def test_recovery_metric_counts_exact_truth():
     assert bench.recovery(wl, tb)["within_1pct"] == {"A": n, "B": 0, "C": n, "all": 0}
     th[:, 2] *= 1.02
     assert bench.recovery(wl, th)["within_1pct"] == {"A": n, "B": n, "C": 0, "all": 0}
+
+
+def test_member_order_reading_for_the_traffic_figure():
+    """bench.member_order_on reads the context's option and, for "auto",
+    applies the library's rule (members in window order when the apertures
+    hold at least 768 traces on average), so that `roofline.traffic` is
+    reported only for the launch form its DRAM capture was taken in."""
+    sys.path.insert(0, ROOT)
+    import types
+
+    import numpy as np
+
+    import bench
+
+    class FakeTT:
+        def __init__(self, value):
+            self.value = value
+
+        def tt_ctx_get_option(self, ctx, option):
+            assert option == "member_order"
+            return self.value
+
+    def problem(aps, per_group=3):
+        ptr = np.concatenate([[0], np.cumsum(aps)]).astype(np.int32)
+        return types.SimpleNamespace(ap_ptr=ptr,
+                                     dom_group=np.repeat(np.arange(len(aps)), per_group))
+
+    long_ap, short_ap = problem([800, 760, 780]), problem([700, 760, 790])
+    assert bench.member_order_on(FakeTT("auto"), None, long_ap) is True    # mean 780
+    assert bench.member_order_on(FakeTT("auto"), None, short_ap) is False  # mean 750
+    assert bench.member_order_on(FakeTT(True), None, short_ap) is True
+    assert bench.member_order_on(FakeTT(False), None, long_ap) is False
+    assert bench.member_order_on(FakeTT("auto"), None, problem([], 0)) is False
+    assert bench.K1_LINE_DRAM_MEMBER_ORDER is True  # the committed capture's form
